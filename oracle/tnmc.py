@@ -1,0 +1,390 @@
+"""Plain FP64 oracle of the TNMH proposal path (test infrastructure only).
+
+Only tests/, __graft_entry__.smoke() and bench.py's CPU legs may use this
+module.  Everything is written for clarity: numpy loops over rows and sites,
+vectorised over samples; numpy's QR / SVD / matmul serve as library steps.
+
+Conventions (Sec. 2, eq. ising):
+  lattice Ly x Lx, open boundaries, site (r, c), row r = 0 is sampled first;
+  Jh[r, c]  bond (r, c)-(r, c+1)   shape (Ly, Lx-1)
+  Jv[r, c]  bond (r, c)-(r+1, c)   shape (Ly-1, Lx)
+  h[r, c]   field                  shape (Ly, Lx)
+  H = -sum h s - sum J s s;   physical index 0 <-> s = -1, 1 <-> s = +1.
+
+Environment of row r (App. A, eq. braket-top-tm-bot, read bottom-up):
+  env_r(sigma_r) approximates the Boltzmann weight of rows r..Ly-1 summed over
+  rows r+1.., including row r's fields and horizontal bonds but not the
+  vertical bonds to row r-1.  It is an MPS  M^(r)_c[a, sigma, b]  built as
+    env_{Ly-1} = exact row weight,
+    env_r      = T_chi[ D_r H_r V_r env_{r+1} ],
+  V_r: sum over row r+1 with the vertical bond weights (no bond growth),
+  D_r: fields, H_r: horizontal bonds as a bond-2 copy MPO (bond doubles),
+  T_chi: "successive SVD" -- a left-to-right QR sweep, then a right-to-left
+  SVD sweep keeping chi_c = min(chi, 2^c, 2^(Lx-c), 2^(Ly-r)) values.
+The conditioned rows above are a product state (the fixed-spin tensors of
+App. A are rank one), so sampling row r uses env_r with site factors
+  f_c(sigma) = exp(beta Jv[r-1, c] s_{r-1, c} sigma).
+Each site conditional is normalised, w_+ / (w_+ + w_-) (Sec. 2, eq.
+pi-approx), after clamping negative weights at zero.
+"""
+import math
+
+import numpy as np
+
+from . import philox
+
+SPIN = np.array([-1.0, 1.0])          # physical index -> spin value
+F_BAD = 1                             # flag: non-positive / non-finite normaliser
+
+
+def bond_dim(chi, Lx, Ly, r, c):
+    """Static bond dimension of bond c (between sites c-1 and c) of env_r."""
+    if c <= 0 or c >= Lx:
+        return 1
+    e = min(c, Lx - c, Ly - r, 30)
+    return min(chi, 1 << e)
+
+
+class Env:
+    """Boundary-MPS row environments of one instance (all FP64)."""
+
+    def __init__(self, Lx, Ly, beta, chi, Jh, Jv, h):
+        self.Lx, self.Ly, self.beta, self.chi = Lx, Ly, beta, chi
+        self.Jh, self.Jv, self.h = Jh, Jv, h
+        self.M = [None] * Ly            # M[r][c]: array (chi_c, 2, chi_{c+1})
+        self.log_scale = np.zeros(Ly)   # log of the factor removed while building row r
+        self.log_lambda = np.zeros(Ly + 1)
+        self.sv = {}                    # (r, c) -> kept singular values / 2-norm of all
+        self.discarded = {}             # (r, c) -> discarded squared weight fraction
+        self.logZ = float("nan")
+
+
+def _check_lattice(Jh, Jv, h):
+    h = np.asarray(h, dtype=np.float64)
+    Ly, Lx = h.shape
+    Jh = np.asarray(Jh, dtype=np.float64).reshape(Ly, max(Lx - 1, 0))
+    Jv = np.asarray(Jv, dtype=np.float64).reshape(max(Ly - 1, 0), Lx)
+    return Jh, Jv, h, Lx, Ly
+
+
+def apply_row_mpo(env_next, Jh, Jv, h, beta, r):
+    """D_r H_r V_r env_{r+1} as an explicit MPS with doubled bonds.
+
+    Left index of site c > 0 is (a, k) -> 2 a + k with k the copied spin
+    index of site c-1; right index of site c < Lx-1 is (b, k') -> 2 b + k'.
+    """
+    Ly, Lx = h.shape
+    P = []
+    for c in range(Lx):
+        if env_next is None:
+            t = np.ones((1, 2, 1))
+        else:
+            W = np.exp(beta * Jv[r, c] * np.outer(SPIN, SPIN))     # W[sigma, sigma']
+            t = np.einsum("ts,asb->atb", W, env_next[c])
+        t = t * np.exp(beta * h[r, c] * SPIN)[None, :, None]
+        Dl, _, Dr = t.shape
+        if c > 0:
+            G = np.exp(beta * Jh[r, c - 1] * np.outer(SPIN, SPIN))  # G[k, sigma]
+            t = np.einsum("asb,ks->aksb", t, G).reshape(Dl * 2, 2, Dr)
+            Dl *= 2
+        if c < Lx - 1:
+            t2 = np.zeros((Dl, 2, Dr, 2))
+            for s in range(2):
+                t2[:, s, :, s] = t[:, s, :]
+            t = t2.reshape(Dl, 2, Dr * 2)
+        P.append(t)
+    return P
+
+
+def truncate_row(P, chi, Lx, Ly, r, env=None):
+    """T_chi: left-to-right QR sweep, then right-to-left SVD sweep (App. A).
+
+    Returns (tensors, log of the removed scale).  Rescalings along the sweeps
+    only move a positive factor into the returned log-scale.
+    """
+    P = list(P)
+    logs = 0.0
+    for c in range(Lx - 1):
+        Dl, _, Dr = P[c].shape
+        Q, R = np.linalg.qr(P[c].reshape(Dl * 2, Dr))
+        P[c] = Q.reshape(Dl, 2, Q.shape[1])
+        sc = np.abs(R).max()
+        if not sc > 0:
+            raise FloatingPointError("row %d: zero environment" % r)
+        logs += math.log(sc)
+        P[c + 1] = np.einsum("ij,jsk->isk", R / sc, P[c + 1])
+    for c in range(Lx - 1, 0, -1):
+        Dl, _, Dr = P[c].shape
+        U, S, Vh = np.linalg.svd(P[c].reshape(Dl, 2 * Dr), full_matrices=False)
+        k = bond_dim(chi, Lx, Ly, r, c)
+        assert k <= S.size
+        P[c] = Vh[:k].reshape(k, 2, Dr)
+        if not S[0] > 0:
+            raise FloatingPointError("row %d: zero environment" % r)
+        if env is not None:
+            tot = float(np.sum(S * S))
+            env.sv[(r, c)] = S[:k] / math.sqrt(tot)
+            env.discarded[(r, c)] = float(np.sum(S[k:] ** 2)) / tot
+        logs += math.log(S[0])
+        P[c - 1] = np.einsum("isj,jk->isk", P[c - 1], U[:, :k] * (S[:k] / S[0]))
+    n0 = float(np.linalg.norm(P[0]))
+    if not n0 > 0:
+        raise FloatingPointError("row %d: zero environment" % r)
+    P[0] = P[0] / n0
+    logs += math.log(n0)
+    return P, logs
+
+
+def build_env(Jh, Jv, h, beta, chi):
+    """All row environments, bottom-up (App. A, eq. braket-top-tm-bot)."""
+    Jh, Jv, h, Lx, Ly = _check_lattice(Jh, Jv, h)
+    env = Env(Lx, Ly, float(beta), int(chi), Jh, Jv, h)
+    nxt = None
+    for r in range(Ly - 1, -1, -1):
+        P = apply_row_mpo(nxt, Jh, Jv, h, beta, r)
+        env.M[r], env.log_scale[r] = truncate_row(P, chi, Lx, Ly, r, env)
+        env.log_lambda[r] = env.log_lambda[r + 1] + env.log_scale[r]
+        nxt = env.M[r]
+    # Z~ = lambda_0 * sum_sigma env_0(sigma): row 0 has no field from above.
+    v = np.ones(1)
+    logv = 0.0
+    for c in range(Lx):
+        v = v @ (env.M[0][c][:, 0, :] + env.M[0][c][:, 1, :])
+        m = np.abs(v).max()
+        if m > 0:
+            v = v / m
+            logv += math.log(m)
+    env.logZ = env.log_lambda[0] + logv + math.log(v[0]) if v[0] > 0 else float("nan")
+    return env
+
+
+def _pow2_normalize(x):
+    """Scale each row of x by the power of two that puts its max |x| in [1, 2)."""
+    m = np.max(np.abs(x), axis=1)
+    _, e = np.frexp(m)
+    e = np.where(m > 0, e - 1, 0)
+    return np.ldexp(x, -e[:, None])
+
+
+def row_fields(env, spins, r):
+    """f[b, c, idx] = exp(beta Jv[r-1, c] s_{r-1, c} SPIN[idx]); ones for r = 0."""
+    B = spins.shape[0]
+    if r == 0:
+        return np.ones((B, env.Lx, 2))
+    up = spins[:, r - 1, :].astype(np.float64)
+    return np.exp(env.beta * (env.Jv[r - 1][None, :, None] * up[:, :, None]) * SPIN[None, None, :])
+
+
+def threshold_plus(pplus, x):
+    """Draw rule: s = +1 iff x < floor(p_+ 2^64) (always when p_+ >= 1)."""
+    ge1 = pplus >= 1.0
+    K = np.where(ge1, 0.0, np.floor(pplus * 2.0 ** 64)).astype(np.uint64)
+    return ge1 | (x < K)
+
+
+def run(env, B, seed=0, sample_offset=0, forced=None, keep=False):
+    """Sequential sampler (forced=None) or evaluator (forced spins [B, Ly, Lx]).
+
+    Returns (spins int8 [B, Ly, Lx], logq [B], energy [B], flags [B]) and,
+    with keep=True, the per-row forward record used by the gradient.
+    """
+    Lx, Ly = env.Lx, env.Ly
+    spins = np.zeros((B, Ly, Lx), dtype=np.int8) if forced is None else np.asarray(forced, dtype=np.int8)
+    logq = np.zeros(B)
+    flags = np.zeros(B, dtype=np.int32)
+    samples = np.uint64(sample_offset) + np.arange(B, dtype=np.uint64)
+    record = []
+    with np.errstate(divide="ignore", invalid="ignore", over="ignore"):
+        for r in range(Ly):
+            M = env.M[r]
+            f = row_fields(env, spins, r)
+            R = [None] * (Lx + 1)
+            R[Lx] = np.ones((B, 1))
+            for c in range(Lx - 1, 0, -1):
+                Y = np.einsum("asb,nb->nas", M[c], R[c + 1])
+                R[c] = _pow2_normalize(Y[:, :, 0] * f[:, c, 0:1] + Y[:, :, 1] * f[:, c, 1:2])
+            Lam = [None] * (Lx + 1)
+            Lam[0] = np.ones((B, 1))
+            wraw = np.zeros((B, Lx, 2))
+            for c in range(Lx):
+                U = np.einsum("na,asb->nsb", Lam[c], M[c])
+                wr = np.einsum("nsb,nb->ns", U, R[c + 1]) * f[:, c, :]
+                wraw[:, c, :] = wr
+                w = np.maximum(wr, 0.0)
+                tot = w[:, 0] + w[:, 1]
+                bad = ~(tot > 0) | ~np.isfinite(tot)
+                pplus = np.where(bad, 0.5, w[:, 1] / tot)
+                pminus = np.where(bad, 0.5, w[:, 0] / tot)
+                if forced is None:
+                    x = philox.draw_words(seed, r * Lx + c, samples)
+                    plus = threshold_plus(pplus, x)
+                    spins[:, r, c] = np.where(plus, 1, -1)
+                else:
+                    plus = spins[:, r, c] > 0
+                logq += np.log(np.where(plus, pplus, pminus))
+                flags |= np.where(bad, F_BAD, 0).astype(np.int32)
+                idx = plus.astype(np.int64)
+                Lam[c + 1] = _pow2_normalize(U[np.arange(B), idx, :] * f[np.arange(B), c, idx][:, None])
+            if keep:
+                record.append((f, R, Lam, wraw))
+    logq = np.where(flags != 0, -np.inf, logq)
+    E = energy(env.Jh, env.Jv, env.h, spins)
+    if keep:
+        return spins, logq, E, flags, record
+    return spins, logq, E, flags
+
+
+def sample(env, B, seed=0, sample_offset=0):
+    """Draw B proposals from q = pi~ (Sec. 2, eqs. pi-approx, tns-prior)."""
+    return run(env, B, seed, sample_offset)
+
+
+def logq(env, spins):
+    """Forced evaluation of log q for given configurations (App. A, last eq.)."""
+    s = np.asarray(spins, dtype=np.int8)
+    return run(env, s.shape[0], forced=s)
+
+
+def energy(Jh, Jv, h, spins):
+    """H(sigma) of eq. ising for a batch of configurations [B, Ly, Lx]."""
+    s = np.asarray(spins, dtype=np.float64)
+    E = -(np.asarray(h)[None] * s).sum(axis=(1, 2))
+    if s.shape[2] > 1:
+        E -= (np.asarray(Jh)[None] * s[:, :, :-1] * s[:, :, 1:]).sum(axis=(1, 2))
+    if s.shape[1] > 1:
+        E -= (np.asarray(Jv)[None] * s[:, :-1, :] * s[:, 1:, :]).sum(axis=(1, 2))
+    return E
+
+
+def init_chains(env, C, seed):
+    """Random +-1 start (Algorithm 1, second step) with its log q and energy."""
+    sp = philox.init_bits(seed, env.Lx * env.Ly, np.arange(C)).reshape(C, env.Ly, env.Lx)
+    _, lq, E, _ = logq(env, sp)
+    return sp, lq, E
+
+
+def mh_accept(beta, lq_prop, E_prop, lq_cur, E_cur, u):
+    """Metropolis-Hastings rule of eq. mh-acc with g(w'|w) = q(w') (eq. tns-prior).
+
+    Delta = -beta (E' - E) + log q(cur) - log q(prop); accept iff the proposal
+    is valid (finite log q) and u < exp(min(0, Delta)).
+    """
+    with np.errstate(invalid="ignore", over="ignore"):
+        d = -beta * (E_prop - E_cur) + (lq_cur - lq_prop)
+        ok = np.isfinite(lq_prop) & ~np.isnan(d)
+        return ok & (u < np.exp(np.minimum(np.where(ok, d, 0.0), 0.0)))
+
+
+def mh_scan(beta, C, T, prop_spins, prop_logq, prop_E, chain_spins, chain_logq, chain_E,
+            seed, step_offset=0):
+    """C chains, chain i consumes proposals i*T .. i*T+T-1 in order (Algorithm 1).
+
+    Returns (accepted [C*T] bool, new chain spins, log q, energy).
+    """
+    chains = np.arange(C)
+    acc = np.zeros(C * T, dtype=bool)
+    lq = np.array(chain_logq, dtype=np.float64)
+    E = np.array(chain_E, dtype=np.float64)
+    last = np.full(C, -1)
+    for j in range(T):
+        t = chains * T + j
+        u = philox.mh_uniform(seed, np.uint64(step_offset + j), chains)
+        a = mh_accept(beta, prop_logq[t], prop_E[t], lq, E, u)
+        acc[t] = a
+        lq = np.where(a, prop_logq[t], lq)
+        E = np.where(a, prop_E[t], E)
+        last = np.where(a, t, last)
+    sp = np.array(chain_spins, copy=True)
+    for i in range(C):
+        if last[i] >= 0:
+            sp[i] = prop_spins[last[i]]
+    return acc, sp, lq, E
+
+
+def logq_grad(env, spins, weights):
+    """Reverse-mode gradient of sum_b weights_b log q(spins_b) w.r.t. every M^(r)_c.
+
+    Follows the forced evaluation step by step: per-site normalised, clamped
+    conditionals, power-of-two rescalings treated as constants.  Samples with
+    a flag or with q = 0 contribute nothing.  Returns (logq, grads) with grads
+    shaped like env.M.
+    """
+    spins = np.asarray(spins, dtype=np.int8)
+    B = spins.shape[0]
+    _, lq, _, flags, rec = run(env, B, forced=spins, keep=True)
+    wts = np.where(np.isfinite(lq) & (flags == 0), np.asarray(weights, dtype=np.float64), 0.0)
+    Lx = env.Lx
+    grads = []
+    for r in range(env.Ly):
+        M = env.M[r]
+        f, R, Lam, wraw = rec[r]
+        s_idx = (spins[:, r, :] > 0).astype(np.int64)
+        G = [np.zeros_like(m) for m in M]
+        Lbar = [np.zeros_like(Lam[c]) for c in range(Lx + 1)]
+        Rbar = [np.zeros_like(R[c]) for c in range(Lx + 1)]
+        ar = np.arange(B)
+        # direct terms of each site's log w(s) - log(w_+ + w_-)
+        for c in range(Lx):
+            w = np.maximum(wraw[:, c, :], 0.0)
+            tot = w[:, 0] + w[:, 1]
+            ws = w[ar, s_idx[:, c]]
+            safe = (wts != 0) & (ws > 0) & (tot > 0)
+            gw = np.zeros((B, 2))
+            inv_tot = np.where(safe, 1.0 / np.where(safe, tot, 1.0), 0.0)
+            gw -= inv_tot[:, None]
+            gw[ar, s_idx[:, c]] += np.where(safe, 1.0 / np.where(safe, ws, 1.0), 0.0)
+            gw *= (wraw[:, c, :] > 0) * wts[:, None] * f[:, c, :]
+            # w(sigma) = f sum_ab Lam[a] M[a, sigma, b] R[b]
+            G[c] += np.einsum("ns,na,nb->asb", gw, Lam[c], R[c + 1])
+            Lbar[c] += np.einsum("ns,asb,nb->na", gw, M[c], R[c + 1])
+            Rbar[c + 1] += np.einsum("ns,na,asb->nb", gw, Lam[c], M[c])
+        # left chain: Lam[c+1] = kappa f(s) Lam[c] M[:, s, :]
+        for c in range(Lx - 1, -1, -1):
+            U = np.einsum("na,asb->nsb", Lam[c], M[c])[ar, s_idx[:, c], :] * f[ar, c, s_idx[:, c]][:, None]
+            kap = _ratio(Lam[c + 1], U)
+            coef = kap * f[ar, c, s_idx[:, c]]
+            Ms = M[c][:, s_idx[:, c], :]                       # (a, n, b)
+            Lbar[c] += np.einsum("n,anb,nb->na", coef, Ms, Lbar[c + 1])
+            for s in range(2):
+                sel = (s_idx[:, c] == s) * coef
+                G[c][:, s, :] += np.einsum("n,na,nb->ab", sel, Lam[c], Lbar[c + 1])
+        # right chain: R[c] = kappa sum_sigma f(sigma) M[:, sigma, :] R[c+1]
+        for c in range(1, Lx):
+            Y = np.einsum("asb,nb->nas", M[c], R[c + 1])
+            raw = Y[:, :, 0] * f[:, c, 0:1] + Y[:, :, 1] * f[:, c, 1:2]
+            kap = _ratio(R[c], raw)
+            Rbar[c + 1] += np.einsum("n,ns,asb,na->nb", kap, f[:, c, :], M[c], Rbar[c])
+            G[c] += np.einsum("n,ns,na,nb->asb", kap, f[:, c, :], Rbar[c], R[c + 1])
+        grads.append(G)
+    return lq, grads
+
+
+def _ratio(scaled, raw):
+    """Per-sample power-of-two factor kappa with scaled = kappa * raw."""
+    m_s = np.max(np.abs(scaled), axis=1)
+    m_r = np.max(np.abs(raw), axis=1)
+    return np.where(m_r > 0, m_s / np.where(m_r > 0, m_r, 1.0), 1.0)
+
+
+def logq_at(env, spins, r, c, delta):
+    """log q after adding `delta` to M^(r)_c (finite-difference helper)."""
+    M0 = env.M[r][c]
+    env.M[r][c] = M0 + delta
+    try:
+        _, lq, _, _ = logq(env, spins)
+    finally:
+        env.M[r][c] = M0
+    return lq
+
+
+def finite_diff_grad(env, spins, weights, r, c, h_rel=1e-6):
+    """Central differences of sum_b weights_b log q_b w.r.t. every entry of M^(r)_c."""
+    M0 = env.M[r][c]
+    h = h_rel * max(np.abs(M0).max(), 1e-300)
+    G = np.zeros_like(M0)
+    w = np.asarray(weights, dtype=np.float64)
+    for idx in np.ndindex(M0.shape):
+        d = np.zeros_like(M0)
+        d[idx] = h
+        G[idx] = (np.dot(w, logq_at(env, spins, r, c, d)) - np.dot(w, logq_at(env, spins, r, c, -d))) / (2 * h)
+    return G
