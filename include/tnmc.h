@@ -1,0 +1,178 @@
+/*
+ * tnmc.h -- C ABI of libtnmc.so, the GB300 (sm_103a) path of the TNMH method of
+ * Frias-Perez, Marien, Perez-Garcia, Banuls, Iblisdir, "Collective Monte Carlo
+ * updates through tensor network renormalization" (arXiv:2104.13264).
+ *
+ * Conventions shared by every entry point
+ *   - Lattice Ly x Lx with open boundaries; site (r, c), row r = 0 first;
+ *     site index r*Lx + c.  Spins are int8 -1/+1, layout [sample][Ly][Lx].
+ *   - Couplings (eq. ising):  H = -sum h s - sum J s s with
+ *       Jh [Ly][Lx-1] bond (r,c)-(r,c+1),  Jv [Ly-1][Lx] bond (r,c)-(r+1,c),
+ *       h  [Ly][Lx]   field; all row-major FP64.
+ *   - Every call returns a tnmc_status.  Argument errors are reported
+ *     synchronously (nothing is launched); tnmc_last_error() then returns a
+ *     thread-local message.  No C++ exception crosses the ABI.
+ *   - Device pointers are caller-owned (for instance torch tensors'
+ *     data_ptr()), host pointers are read before the call returns.  Work is
+ *     enqueued on `stream` (a cudaStream_t; NULL = legacy default stream).
+ *   - A tnmc_env is opaque and library-owned; free it with tnmc_env_free.
+ *     Calls that use one env share its device scratch, so they must be
+ *     ordered on one stream (calls that overlap on the GPU race).
+ *   - Numerical trouble found on the device (a non-positive or non-finite
+ *     conditional normaliser, a zero environment) is reported per sample in
+ *     `flags` and in the env's status word, read with tnmc_env_status.
+ *   - Random numbers come from Philox4x32-10 (Salmon et al., SC'11) keyed by
+ *     the 64-bit seed; counters:
+ *       draw of (site, sample) (site/2, sample_lo, sample_hi, 0), words
+ *           (0,1) for even sites, (2,3) for odd ones, as x = lo | hi << 32;
+ *           spin = +1 iff x < floor(p_+ 2^64)  (always when p_+ >= 1);
+ *       MH uniform of proposal t of chain i  (t_lo, t_hi, i, 1), words (0,1),
+ *           u = (x >> 11) 2^-53;
+ *       random start of chain i  (site/128, i_lo, i_hi, 2), bit site % 128.
+ */
+#ifndef TNMC_H
+#define TNMC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TNMC_OK = 0,
+  TNMC_E_INVALID_ARG = 1,
+  TNMC_E_NOMEM = 2,
+  TNMC_E_CUDA = 3,
+  TNMC_E_NUMERIC = 4,
+  TNMC_E_TIMEOUT = 5,
+  TNMC_E_UNSUPPORTED = 6
+} tnmc_status;
+
+/* Arithmetic of the sampler copy of the environment (the builder is always FP64). */
+typedef enum { TNMC_F64 = 0, TNMC_F32 = 1, TNMC_BF16 = 2 } tnmc_precision;
+
+/* Per-sample flag bits. */
+#define TNMC_FLAG_NUMERIC 1
+
+typedef struct tnmc_env tnmc_env;
+
+typedef struct {
+  int Lx, Ly;
+  const double* Jh; /* host [Ly][Lx-1] */
+  const double* Jv; /* host [Ly-1][Lx] */
+  const double* h;  /* host [Ly][Lx]   */
+} tnmc_lattice;
+
+typedef struct {
+  int Lx, Ly, chi;
+  int pad;                /* P: padded bond stride of every stored tensor          */
+  int precision_mask;     /* bit (1 << p) set when the sampler copy p is present   */
+  int integer_couplings;  /* 1 when every J and h is an integer                    */
+  double beta;
+  double logZ;            /* log Z~ of the truncated contraction                   */
+  int64_t bytes;          /* device bytes held by the env                          */
+} tnmc_env_info_t;
+
+/* Thread-local text of the last error (empty string if none). */
+const char* tnmc_last_error(void);
+
+/*
+ * Build the chi-truncated boundary-MPS row environments of one instance in
+ * FP64 on the GPU (App. A, eq. braket-top-tm-bot; "successive SVD").
+ *   env_{Ly-1} is row Ly-1's exact weight; for r < Ly-1
+ *   env_r = T_chi[ D_r H_r V_r env_{r+1} ]:  V_r sums row r+1 with the
+ *   vertical bond weights, D_r applies the fields, H_r the horizontal bonds
+ *   (a bond-2 copy MPO), T_chi is a left-to-right Householder QR sweep then a
+ *   right-to-left one-sided Jacobi SVD sweep keeping
+ *   chi_c = min(chi, 2^c, 2^(Lx-c), 2^(Ly-r)) values per bond.
+ * lat         host lattice (Lx, Ly >= 1; Jh, Jv may be NULL when their size is 0)
+ * beta        inverse temperature, finite, >= 0
+ * chi         1 <= chi <= 64
+ * precision_mask  bit (1 << TNMC_F64 | 1 << TNMC_F32 | 1 << TNMC_BF16): which
+ *             sampler copies to derive (FP64 is always kept)
+ * out         receives the new env (device memory allocated here)
+ * Asynchronous on `stream`; tnmc_env_info / tnmc_env_export synchronise it.
+ */
+tnmc_status tnmc_build_env(const tnmc_lattice* lat, double beta, int chi, int precision_mask,
+                           void* stream, tnmc_env** out);
+
+tnmc_status tnmc_env_free(tnmc_env* env);
+
+/* Synchronises the env's build stream and fills `info`. */
+tnmc_status tnmc_env_info(const tnmc_env* env, tnmc_env_info_t* info);
+
+/*
+ * Copy the FP64 environment to host memory (synchronous).  Any pointer may be NULL.
+ * tensors    [Ly][Lx][P][2][P]  M^(r)_c[a][sigma][b], zero outside the bond dims
+ * log_scale  [Ly]   log of the factor removed while building row r
+ * sv         [Ly][Lx+1][P]  kept singular values at bond c divided by the 2-norm
+ *                           of all singular values of that SVD step (0 elsewhere)
+ * discarded  [Ly][Lx+1]     discarded squared-weight fraction at bond c
+ * bond_dims  [Ly][Lx+1]     chi_c^(r)
+ */
+tnmc_status tnmc_env_export(const tnmc_env* env, double* tensors, double* log_scale, double* sv,
+                            double* discarded, int32_t* bond_dims);
+
+/* Synchronises and reads the env's device status word (0 = clean; else tnmc_status). */
+tnmc_status tnmc_env_status(const tnmc_env* env, int32_t* status);
+
+/*
+ * Draw B independent proposals from q = pi~ (Sec. 2, eqs. bayes, pi-approx,
+ * tns-prior): raster order, one site at a time, each conditional
+ *   w(s) = f_c(s) <Lambda_c M_c[s], R_{c+1}>,  clamped at 0 and normalised,
+ * with f_c(s) = exp(beta Jv[r-1][c] s_{r-1,c} s) (the rows above are a
+ * product state, App. A).  Also returns the exact log q of each draw and its
+ * energy H (eq. ising; exact integers when all couplings are integers).
+ * precision   which sampler copy to use (must be present in the env)
+ * B           number of proposals, >= 0; sample index of row b is sample_offset + b
+ * spins       device int8 [B][Ly][Lx] (output)
+ * logq        device double [B] (output; -inf for flagged samples)
+ * energy      device double [B] (output)
+ * flags       device int32 [B] or NULL (output; TNMC_FLAG_NUMERIC)
+ * The first call on an env may allocate device scratch for the per-sample
+ * right-vector stacks.
+ */
+tnmc_status tnmc_sample(const tnmc_env* env, int precision, int64_t B, uint64_t seed,
+                        uint64_t sample_offset, int8_t* spins, double* logq, double* energy,
+                        int32_t* flags, void* stream);
+
+/*
+ * Forced ("teacher") evaluation of log q and H for given configurations
+ * (App. A, product of conditional ratios); same arithmetic as tnmc_sample.
+ * spins       device int8 [B][Ly][Lx], values -1/+1 (input)
+ */
+tnmc_status tnmc_logq(const tnmc_env* env, int precision, int64_t B, const int8_t* spins,
+                      double* logq, double* energy, int32_t* flags, void* stream);
+
+/*
+ * Random +-1 start of C chains (Algorithm 1, second step) with their forced
+ * log q (sampler copy `precision`) and energy.
+ */
+tnmc_status tnmc_init_chains(const tnmc_env* env, int precision, int64_t C, uint64_t seed,
+                             int8_t* chain_spins, double* chain_logq, double* chain_energy,
+                             void* stream);
+
+/*
+ * Metropolis-Hastings scan (eq. mh-acc with g(w'|w) = q(w'), Algorithm 1):
+ * chain i consumes proposals i*T .. i*T+T-1 in order.  For proposal t
+ *   Delta = -beta (E_t - E_cur) + log q_cur - log q_t,
+ *   accept iff log q_t is finite and u < exp(min(0, Delta)),
+ * u from the MH stream at step (step_offset + j).  On exit each chain holds
+ * its last accepted proposal (spins, log q, energy).
+ * prop_*      device [C*T] (spins [C*T][Ly][Lx])
+ * chain_*     device [C] in/out (spins [C][Ly][Lx])
+ * accepted    device uint8 [C*T] or NULL (output)
+ * n_accepted  device int64 scalar or NULL; the number accepted is ADDED to it
+ */
+tnmc_status tnmc_mh_step(const tnmc_env* env, int64_t C, int64_t T, const int8_t* prop_spins,
+                         const double* prop_logq, const double* prop_energy, int8_t* chain_spins,
+                         double* chain_logq, double* chain_energy, uint64_t seed,
+                         uint64_t step_offset, uint8_t* accepted, int64_t* n_accepted,
+                         void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TNMC_H */

@@ -182,17 +182,22 @@ def threshold_plus(pplus, x):
     return ge1 | (x < K)
 
 
-def run(env, B, seed=0, sample_offset=0, forced=None, keep=False):
+def run(env, B, seed=0, sample_offset=0, forced=None, keep=False, samples=None):
     """Sequential sampler (forced=None) or evaluator (forced spins [B, Ly, Lx]).
 
-    Returns (spins int8 [B, Ly, Lx], logq [B], energy [B], flags [B]) and,
-    with keep=True, the per-row forward record used by the gradient.
+    Sample b uses Philox sample index sample_offset + b, or samples[b] when an
+    explicit index array is given.  Returns (spins int8 [B, Ly, Lx], logq [B],
+    energy [B], flags [B]) and, with keep=True, the per-row forward record
+    used by the gradient.
     """
     Lx, Ly = env.Lx, env.Ly
     spins = np.zeros((B, Ly, Lx), dtype=np.int8) if forced is None else np.asarray(forced, dtype=np.int8)
     logq = np.zeros(B)
     flags = np.zeros(B, dtype=np.int32)
-    samples = np.uint64(sample_offset) + np.arange(B, dtype=np.uint64)
+    if samples is None:
+        samples = np.uint64(sample_offset) + np.arange(B, dtype=np.uint64)
+    else:
+        samples = np.asarray(samples, dtype=np.uint64)
     record = []
     with np.errstate(divide="ignore", invalid="ignore", over="ignore"):
         for r in range(Ly):
@@ -234,9 +239,9 @@ def run(env, B, seed=0, sample_offset=0, forced=None, keep=False):
     return spins, logq, E, flags
 
 
-def sample(env, B, seed=0, sample_offset=0):
+def sample(env, B, seed=0, sample_offset=0, samples=None):
     """Draw B proposals from q = pi~ (Sec. 2, eqs. pi-approx, tns-prior)."""
-    return run(env, B, seed, sample_offset)
+    return run(env, B, seed, sample_offset, samples=samples)
 
 
 def logq(env, spins):

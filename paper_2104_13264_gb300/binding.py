@@ -1,0 +1,197 @@
+"""ctypes binding of libtnmc.so (argument marshalling only).
+
+Every computation happens in the CUDA library; this module passes pointers
+and sizes.  Device memory comes from torch tensors; calls are enqueued on the
+current torch CUDA stream unless one is given.  If the library is missing,
+``lib()`` raises: there is no fallback path.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libtnmc.so")
+
+F64, F32, BF16 = 0, 1, 2
+PRECISIONS = {"f64": F64, "f32": F32, "bf16": BF16}
+FLAG_NUMERIC = 1
+
+_lib = None
+
+
+class TnmcError(RuntimeError):
+    pass
+
+
+class _Lattice(ctypes.Structure):
+    _fields_ = [("Lx", ctypes.c_int), ("Ly", ctypes.c_int), ("Jh", ctypes.c_void_p),
+                ("Jv", ctypes.c_void_p), ("h", ctypes.c_void_p)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("Lx", ctypes.c_int), ("Ly", ctypes.c_int), ("chi", ctypes.c_int), ("pad", ctypes.c_int),
+                ("precision_mask", ctypes.c_int), ("integer_couplings", ctypes.c_int),
+                ("beta", ctypes.c_double), ("logZ", ctypes.c_double), ("bytes", ctypes.c_int64)]
+
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_U64 = ctypes.c_uint64
+_INT = ctypes.c_int
+
+SIGNATURES = {
+    "tnmc_last_error": ([], ctypes.c_char_p),
+    "tnmc_build_env": ([ctypes.POINTER(_Lattice), ctypes.c_double, _INT, _INT, _P, ctypes.POINTER(_P)], _INT),
+    "tnmc_env_free": ([_P], _INT),
+    "tnmc_env_info": ([_P, ctypes.POINTER(_Info)], _INT),
+    "tnmc_env_export": ([_P, _P, _P, _P, _P, _P], _INT),
+    "tnmc_env_status": ([_P, ctypes.POINTER(ctypes.c_int32)], _INT),
+    "tnmc_sample": ([_P, _INT, _I64, _U64, _U64, _P, _P, _P, _P, _P], _INT),
+    "tnmc_logq": ([_P, _INT, _I64, _P, _P, _P, _P, _P], _INT),
+    "tnmc_init_chains": ([_P, _INT, _I64, _U64, _P, _P, _P, _P], _INT),
+    "tnmc_mh_step": ([_P, _I64, _I64, _P, _P, _P, _P, _P, _P, _U64, _U64, _P, _P, _P], _INT),
+}
+
+
+def lib():
+    """Open libtnmc.so (once).  Raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise TnmcError("libtnmc.so not found at %s: run `python -m paper_2104_13264_gb300.build`" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != 0:
+        msg = lib().tnmc_last_error().decode(errors="replace")
+        raise TnmcError("tnmc status %d: %s" % (status, msg))
+
+
+def _stream(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+class Env:
+    """FP64-built row environments of one instance (owned by the library)."""
+
+    def __init__(self, Jh, Jv, h, beta, chi, precisions=("f64",), stream=None):
+        h = np.ascontiguousarray(h, dtype=np.float64)
+        Ly, Lx = h.shape
+        Jh = np.ascontiguousarray(np.asarray(Jh, dtype=np.float64).reshape(Ly, max(Lx - 1, 0)))
+        Jv = np.ascontiguousarray(np.asarray(Jv, dtype=np.float64).reshape(max(Ly - 1, 0), Lx))
+        self.Lx, self.Ly, self.beta, self.chi = Lx, Ly, float(beta), int(chi)
+        mask = 0
+        for p in precisions:
+            mask |= 1 << PRECISIONS[p]
+        lat = _Lattice(Lx, Ly, Jh.ctypes.data if Jh.size else None, Jv.ctypes.data if Jv.size else None,
+                       h.ctypes.data)
+        out = ctypes.c_void_p()
+        self._h = None
+        _check(lib().tnmc_build_env(ctypes.byref(lat), self.beta, self.chi, mask, _stream(stream), ctypes.byref(out)))
+        self._h = out
+
+    @classmethod
+    def from_instance(cls, inst, precisions=("f64",), chi=None, stream=None):
+        return cls(inst.Jh, inst.Jv, inst.h, inst.beta, inst.chi if chi is None else chi, precisions, stream)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self):
+        i = _Info()
+        _check(lib().tnmc_env_info(self._h, ctypes.byref(i)))
+        return {k: getattr(i, k) for k, _ in _Info._fields_}
+
+    def export(self):
+        """Host copies: tensors [Ly][Lx][P][2][P], log_scale, sv, discarded, bond_dims."""
+        inf = self.info()
+        P, Lx, Ly = inf["pad"], self.Lx, self.Ly
+        T = np.zeros((Ly, Lx, P, 2, P))
+        ls = np.zeros(Ly)
+        sv = np.zeros((Ly, Lx + 1, P))
+        dsc = np.zeros((Ly, Lx + 1))
+        bd = np.zeros((Ly, Lx + 1), dtype=np.int32)
+        _check(lib().tnmc_env_export(self._h, T.ctypes.data, ls.ctypes.data, sv.ctypes.data, dsc.ctypes.data,
+                                     bd.ctypes.data))
+        return {"tensors": T, "log_scale": ls, "sv": sv, "discarded": dsc, "bond_dims": bd, "logZ": inf["logZ"]}
+
+    def status(self):
+        s = ctypes.c_int32()
+        _check(lib().tnmc_env_status(self._h, ctypes.byref(s)))
+        return s.value
+
+    def free(self):
+        if self._h is not None and self._h.value:
+            lib().tnmc_env_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def sample(env, B, seed=0, sample_offset=0, precision="f64", out=None, stream=None):
+    """Draw B proposals: returns (spins int8 [B,Ly,Lx], logq [B], energy [B], flags [B]) on cuda."""
+    import torch
+    dev = torch.device("cuda")
+    if out is None:
+        out = (torch.empty((B, env.Ly, env.Lx), dtype=torch.int8, device=dev),
+               torch.empty(B, dtype=torch.float64, device=dev), torch.empty(B, dtype=torch.float64, device=dev),
+               torch.empty(B, dtype=torch.int32, device=dev))
+    sp, lq, E, fl = out
+    _check(lib().tnmc_sample(env.handle, PRECISIONS[precision], B, seed, sample_offset, _ptr(sp), _ptr(lq),
+                             _ptr(E), _ptr(fl), _stream(stream)))
+    return sp, lq, E, fl
+
+
+def logq(env, spins, precision="f64", stream=None):
+    """Forced log q and energy of configurations spins (int8 cuda tensor [B,Ly,Lx])."""
+    import torch
+    spins = spins.contiguous()
+    B = spins.shape[0]
+    lq = torch.empty(B, dtype=torch.float64, device=spins.device)
+    E = torch.empty(B, dtype=torch.float64, device=spins.device)
+    fl = torch.empty(B, dtype=torch.int32, device=spins.device)
+    _check(lib().tnmc_logq(env.handle, PRECISIONS[precision], B, _ptr(spins), _ptr(lq), _ptr(E), _ptr(fl),
+                           _stream(stream)))
+    return lq, E, fl
+
+
+def init_chains(env, C, seed=0, precision="f64", stream=None):
+    import torch
+    dev = torch.device("cuda")
+    sp = torch.empty((C, env.Ly, env.Lx), dtype=torch.int8, device=dev)
+    lq = torch.empty(C, dtype=torch.float64, device=dev)
+    E = torch.empty(C, dtype=torch.float64, device=dev)
+    _check(lib().tnmc_init_chains(env.handle, PRECISIONS[precision], C, seed, _ptr(sp), _ptr(lq), _ptr(E),
+                                  _stream(stream)))
+    return sp, lq, E
+
+
+def mh_step(env, C, T, prop, chain, seed=0, step_offset=0, accepted=None, n_accepted=None, stream=None):
+    """MH scan; prop = (spins, logq, energy) [C*T], chain = (spins, logq, energy) [C] updated in place."""
+    import torch
+    ps, plq, pE = prop
+    cs, clq, cE = chain
+    if accepted is None:
+        accepted = torch.empty(C * T, dtype=torch.uint8, device=plq.device)
+    _check(lib().tnmc_mh_step(env.handle, C, T, _ptr(ps), _ptr(plq), _ptr(pE), _ptr(cs), _ptr(clq), _ptr(cE),
+                              seed, step_offset, _ptr(accepted), _ptr(n_accepted), _stream(stream)))
+    return accepted

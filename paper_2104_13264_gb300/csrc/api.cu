@@ -1,0 +1,277 @@
+// C-ABI entry points of libtnmc: argument checking, device memory of the
+// environment, and the launches.  No C++ exception crosses the boundary.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+
+static thread_local char g_err[512] = "";
+
+void tnmc_set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+#define CHECK_ARG(cond, ...)          \
+  do {                                \
+    if (!(cond)) {                    \
+      tnmc_set_error(__VA_ARGS__);    \
+      return TNMC_E_INVALID_ARG;      \
+    }                                 \
+  } while (0)
+
+namespace {
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+bool is_integer_array(const double* p, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (p[i] != floor(p[i])) return false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* tnmc_last_error(void) { return g_err; }
+
+tnmc_status tnmc_build_env(const tnmc_lattice* lat, double beta, int chi, int precision_mask, void* stream,
+                           tnmc_env** out) {
+  using namespace tnmc;
+  g_err[0] = 0;
+  CHECK_ARG(lat && out, "lat and out must be non-null");
+  *out = nullptr;
+  const int Lx = lat->Lx, Ly = lat->Ly;
+  CHECK_ARG(Lx >= 1 && Ly >= 1 && Lx <= 4096 && Ly <= 4096, "lattice %d x %d out of range", Ly, Lx);
+  CHECK_ARG(chi >= 1 && chi <= kMaxChi, "chi = %d must be in [1, %d]", chi, kMaxChi);
+  CHECK_ARG(isfinite(beta) && beta >= 0.0, "beta must be finite and >= 0");
+  CHECK_ARG(lat->h, "h must be non-null");
+  CHECK_ARG(Lx == 1 || lat->Jh, "Jh must be non-null when Lx > 1");
+  CHECK_ARG(Ly == 1 || lat->Jv, "Jv must be non-null when Ly > 1");
+  CHECK_ARG((precision_mask & ~7) == 0, "unknown precision bits in mask 0x%x", precision_mask);
+  const size_t nJh = (size_t)Ly * (Lx - 1), nJv = (size_t)(Ly - 1) * Lx, nh = (size_t)Ly * Lx;
+  for (size_t i = 0; i < nJh; ++i) CHECK_ARG(isfinite(lat->Jh[i]), "Jh[%zu] is not finite", i);
+  for (size_t i = 0; i < nJv; ++i) CHECK_ARG(isfinite(lat->Jv[i]), "Jv[%zu] is not finite", i);
+  for (size_t i = 0; i < nh; ++i) CHECK_ARG(isfinite(lat->h[i]), "h[%zu] is not finite", i);
+  const int mask = precision_mask | (1 << TNMC_F64);
+  // padded bond stride
+  int maxb = 1;
+  for (int r = 0; r < Ly; ++r)
+    for (int c = 0; c <= Lx; ++c) {
+      const int b = bond_dim_host(chi, Lx, Ly, r, c);
+      if (b > maxb) maxb = b;
+    }
+  const int P = pad4(maxb);
+  const size_t ntens = (size_t)Lx * Ly;
+  const size_t tens = ntens * P * 2 * P;
+  // arena layout
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off += align256(bytes);
+    return o;
+  };
+  const size_t oJh = take((nJh ? nJh : 1) * 8), oJv = take((nJv ? nJv : 1) * 8), oh = take(nh * 8);
+  const size_t ofe = take(nh * 2 * 8), ofe32 = take(nh * 2 * 4);
+  const size_t obond = take((size_t)Ly * (Lx + 1) * 4);
+  const size_t oM64 = take(tens * 8), oR64 = take(tens * 8);
+  const size_t oL32 = (mask & (1 << TNMC_F32)) ? take(tens * 4) : 0;
+  const size_t oR32 = (mask & (1 << TNMC_F32)) ? take(tens * 4) : 0;
+  const size_t oL16 = (mask & (1 << TNMC_BF16)) ? take(tens * 2) : 0;
+  const size_t oR16 = (mask & (1 << TNMC_BF16)) ? take(tens * 2) : 0;
+  const size_t ols = take((size_t)Ly * 8), osv = take((size_t)Ly * (Lx + 1) * P * 8);
+  const size_t odisc = take((size_t)Ly * (Lx + 1) * 8), ologZ = take(8), ostat = take(8);
+  const size_t total = off;
+
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  tnmc_env* env = new (std::nothrow) tnmc_env();
+  if (!env) {
+    tnmc_set_error("host allocation failed");
+    return TNMC_E_NOMEM;
+  }
+  char* base = nullptr;
+  if (cudaMalloc(&base, total) != cudaSuccess) {
+    (void)cudaGetLastError();
+    delete env;
+    tnmc_set_error("cannot allocate %zu bytes for the environment", total);
+    return TNMC_E_NOMEM;
+  }
+  env->arena = base;
+  env->arena_bytes = total;
+  env->precision_mask = mask;
+  env->build_stream = s;
+  DeviceEnv& d = env->d;
+  d.Lx = Lx;
+  d.Ly = Ly;
+  d.chi = chi;
+  d.P = P;
+  d.beta = beta;
+  d.integer_couplings = is_integer_array(lat->h, nh) && (nJh == 0 || is_integer_array(lat->Jh, nJh)) &&
+                        (nJv == 0 || is_integer_array(lat->Jv, nJv));
+  d.Jh = reinterpret_cast<const double*>(base + oJh);
+  d.Jv = reinterpret_cast<const double*>(base + oJv);
+  d.h = reinterpret_cast<const double*>(base + oh);
+  d.fe = reinterpret_cast<const double*>(base + ofe);
+  d.fe32 = reinterpret_cast<const float*>(base + ofe32);
+  d.bond = reinterpret_cast<const int32_t*>(base + obond);
+  d.M64 = reinterpret_cast<const double*>(base + oM64);
+  d.R64 = reinterpret_cast<const double*>(base + oR64);
+  d.L32 = oL32 ? reinterpret_cast<const float*>(base + oL32) : nullptr;
+  d.R32 = oR32 ? reinterpret_cast<const float*>(base + oR32) : nullptr;
+  d.L16 = oL16 ? reinterpret_cast<const __nv_bfloat16*>(base + oL16) : nullptr;
+  d.R16 = oR16 ? reinterpret_cast<const __nv_bfloat16*>(base + oR16) : nullptr;
+  d.status = reinterpret_cast<int32_t*>(base + ostat);
+  env->log_scale = reinterpret_cast<double*>(base + ols);
+  env->sv = reinterpret_cast<double*>(base + osv);
+  env->discarded = reinterpret_cast<double*>(base + odisc);
+  env->logZ = reinterpret_cast<double*>(base + ologZ);
+
+  tnmc_status st = TNMC_OK;
+  void* work = nullptr;
+  const size_t wbytes = tnmc_build_work_bytes(Lx, Ly, P);
+  do {
+    if (cudaMemsetAsync(base, 0, total, s) != cudaSuccess) { st = TNMC_E_CUDA; break; }
+    if (nJh && cudaMemcpyAsync(const_cast<double*>(d.Jh), lat->Jh, nJh * 8, cudaMemcpyHostToDevice, s) != cudaSuccess) { st = TNMC_E_CUDA; break; }
+    if (nJv && cudaMemcpyAsync(const_cast<double*>(d.Jv), lat->Jv, nJv * 8, cudaMemcpyHostToDevice, s) != cudaSuccess) { st = TNMC_E_CUDA; break; }
+    if (cudaMemcpyAsync(const_cast<double*>(d.h), lat->h, nh * 8, cudaMemcpyHostToDevice, s) != cudaSuccess) { st = TNMC_E_CUDA; break; }
+    // the host arrays may be released as soon as this call returns
+    if (cudaStreamSynchronize(s) != cudaSuccess) { st = TNMC_E_CUDA; break; }
+    if (cudaMallocAsync(&work, wbytes, s) != cudaSuccess) {
+      work = nullptr;
+      st = TNMC_E_NOMEM;
+      tnmc_set_error("cannot allocate %zu bytes of builder scratch", wbytes);
+      break;
+    }
+    st = tnmc_launch_build(env, s, work, wbytes);
+    if (st != TNMC_OK) break;
+    st = tnmc_launch_derive(env, mask, s);
+  } while (0);
+  if (work) (void)cudaFreeAsync(work, s);
+  if (st != TNMC_OK) {
+    if (st == TNMC_E_CUDA && !g_err[0]) tnmc_set_error("CUDA error while building: %s", cudaGetErrorString(cudaGetLastError()));
+    (void)cudaStreamSynchronize(s);
+    cudaFree(base);
+    delete env;
+    return st;
+  }
+  *out = env;
+  return TNMC_OK;
+}
+
+tnmc_status tnmc_env_free(tnmc_env* env) {
+  if (!env) return TNMC_OK;
+  cudaDeviceSynchronize();
+  if (env->scratch.ptr) cudaFree(env->scratch.ptr);
+  if (env->arena) cudaFree(env->arena);
+  delete env;
+  return TNMC_OK;
+}
+
+tnmc_status tnmc_env_info(const tnmc_env* env, tnmc_env_info_t* info) {
+  CHECK_ARG(env && info, "env and info must be non-null");
+  TNMC_CUDA_TRY(cudaStreamSynchronize(env->build_stream));
+  double logZ = 0.0;
+  TNMC_CUDA_TRY(cudaMemcpy(&logZ, env->logZ, sizeof(double), cudaMemcpyDeviceToHost));
+  info->Lx = env->d.Lx;
+  info->Ly = env->d.Ly;
+  info->chi = env->d.chi;
+  info->pad = env->d.P;
+  info->precision_mask = env->precision_mask;
+  info->integer_couplings = env->d.integer_couplings;
+  info->beta = env->d.beta;
+  info->logZ = logZ;
+  info->bytes = (int64_t)(env->arena_bytes + env->scratch.bytes);
+  return TNMC_OK;
+}
+
+tnmc_status tnmc_env_export(const tnmc_env* env, double* tensors, double* log_scale, double* sv, double* discarded,
+                            int32_t* bond_dims) {
+  CHECK_ARG(env, "env must be non-null");
+  const tnmc::DeviceEnv& d = env->d;
+  TNMC_CUDA_TRY(cudaStreamSynchronize(env->build_stream));
+  const size_t tens = (size_t)d.Lx * d.Ly * d.P * 2 * d.P;
+  if (tensors) TNMC_CUDA_TRY(cudaMemcpy(tensors, d.M64, tens * 8, cudaMemcpyDeviceToHost));
+  if (log_scale) TNMC_CUDA_TRY(cudaMemcpy(log_scale, env->log_scale, (size_t)d.Ly * 8, cudaMemcpyDeviceToHost));
+  if (sv) TNMC_CUDA_TRY(cudaMemcpy(sv, env->sv, (size_t)d.Ly * (d.Lx + 1) * d.P * 8, cudaMemcpyDeviceToHost));
+  if (discarded) TNMC_CUDA_TRY(cudaMemcpy(discarded, env->discarded, (size_t)d.Ly * (d.Lx + 1) * 8, cudaMemcpyDeviceToHost));
+  if (bond_dims) TNMC_CUDA_TRY(cudaMemcpy(bond_dims, d.bond, (size_t)d.Ly * (d.Lx + 1) * 4, cudaMemcpyDeviceToHost));
+  return TNMC_OK;
+}
+
+tnmc_status tnmc_env_status(const tnmc_env* env, int32_t* status) {
+  CHECK_ARG(env && status, "env and status must be non-null");
+  TNMC_CUDA_TRY(cudaDeviceSynchronize());
+  TNMC_CUDA_TRY(cudaMemcpy(status, env->d.status, sizeof(int32_t), cudaMemcpyDeviceToHost));
+  return TNMC_OK;
+}
+
+static tnmc_status check_precision(const tnmc_env* env, int precision) {
+  CHECK_ARG(precision >= 0 && precision <= 2, "unknown precision %d", precision);
+  if (!(env->precision_mask & (1 << precision))) {
+    tnmc_set_error("the env was built without the sampler copy for precision %d", precision);
+    return TNMC_E_UNSUPPORTED;
+  }
+  return TNMC_OK;
+}
+
+tnmc_status tnmc_sample(const tnmc_env* env, int precision, int64_t B, uint64_t seed, uint64_t sample_offset,
+                        int8_t* spins, double* logq, double* energy, int32_t* flags, void* stream) {
+  g_err[0] = 0;
+  CHECK_ARG(env, "env must be non-null");
+  CHECK_ARG(B >= 0, "B must be >= 0");
+  CHECK_ARG(B == 0 || (spins && logq && energy), "spins, logq and energy must be non-null");
+  tnmc_status st = check_precision(env, precision);
+  if (st != TNMC_OK) return st;
+  return tnmc_launch_sample(env, precision, B, seed, sample_offset, nullptr, spins, logq, energy, flags,
+                            static_cast<cudaStream_t>(stream));
+}
+
+tnmc_status tnmc_logq(const tnmc_env* env, int precision, int64_t B, const int8_t* spins, double* logq,
+                      double* energy, int32_t* flags, void* stream) {
+  g_err[0] = 0;
+  CHECK_ARG(env, "env must be non-null");
+  CHECK_ARG(B >= 0, "B must be >= 0");
+  CHECK_ARG(B == 0 || (spins && logq && energy), "spins, logq and energy must be non-null");
+  tnmc_status st = check_precision(env, precision);
+  if (st != TNMC_OK) return st;
+  return tnmc_launch_sample(env, precision, B, 0, 0, spins, nullptr, logq, energy, flags,
+                            static_cast<cudaStream_t>(stream));
+}
+
+tnmc_status tnmc_init_chains(const tnmc_env* env, int precision, int64_t C, uint64_t seed, int8_t* chain_spins,
+                             double* chain_logq, double* chain_energy, void* stream) {
+  g_err[0] = 0;
+  CHECK_ARG(env, "env must be non-null");
+  CHECK_ARG(C >= 0 && C < ((int64_t)1 << 32), "C out of range");
+  CHECK_ARG(C == 0 || (chain_spins && chain_logq && chain_energy), "chain arrays must be non-null");
+  tnmc_status st = check_precision(env, precision);
+  if (st != TNMC_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  st = tnmc_launch_init_bits(env, C, seed, chain_spins, s);
+  if (st != TNMC_OK) return st;
+  return tnmc_launch_sample(env, precision, C, 0, 0, chain_spins, nullptr, chain_logq, chain_energy, nullptr, s);
+}
+
+tnmc_status tnmc_mh_step(const tnmc_env* env, int64_t C, int64_t T, const int8_t* prop_spins,
+                         const double* prop_logq, const double* prop_energy, int8_t* chain_spins,
+                         double* chain_logq, double* chain_energy, uint64_t seed, uint64_t step_offset,
+                         uint8_t* accepted, int64_t* n_accepted, void* stream) {
+  g_err[0] = 0;
+  CHECK_ARG(env, "env must be non-null");
+  CHECK_ARG(C >= 0 && C < ((int64_t)1 << 32) && T >= 0, "C or T out of range");
+  CHECK_ARG(C == 0 || T == 0 ||
+                (prop_spins && prop_logq && prop_energy && chain_spins && chain_logq && chain_energy),
+            "proposal and chain arrays must be non-null");
+  return tnmc_launch_mh(env, C, T, prop_spins, prop_logq, prop_energy, chain_spins, chain_logq, chain_energy, seed,
+                        step_offset, accepted, n_accepted, static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

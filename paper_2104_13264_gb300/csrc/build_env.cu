@@ -1,0 +1,633 @@
+// FP64 boundary-MPS builder (App. A, eq. braket-top-tm-bot; "successive SVD").
+//
+// One CTA builds every row environment of one instance, bottom-up:
+//   env_{Ly-1} = exact weight of row Ly-1;  env_r = T_chi[ D_r H_r V_r env_{r+1} ].
+// Per row:
+//   1. MPO application (V_r vertical bonds, D_r fields, H_r horizontal bonds as a
+//      bond-2 copy MPO): site c becomes a (Dl x 2 x Dr) tensor with doubled bonds;
+//      the right index (b, k') carries a copy k' of the site's own spin.
+//   2. Left-to-right Householder QR sweep.  Because k' copies the spin, each
+//      site matrix (Dl*2) x Dr is block diagonal in (s, k'), so it is factored as
+//      two (Dl x Dr/2) QRs; R is absorbed into the next site.
+//   3. Right-to-left SVD sweep: one-sided Jacobi (Hestenes) on the rows of the
+//      (Dl x 2 Dr) site matrix, keep the chi_c largest rows (= sigma_i v_i^T), the
+//      normalised rows become the right-orthonormal site, U S = A V_k is absorbed
+//      into the left neighbour.
+//   4. Site 0 is divided by its Frobenius norm; every positive factor removed on
+//      the way is accumulated in log_scale[r].
+// Working tensors live in global scratch slots (L2 resident); the linear algebra
+// of one site runs in shared memory.  All arithmetic is FP64.
+#include <math.h>
+
+#include "common.cuh"
+
+namespace tnmc {
+namespace {
+
+constexpr int kBuildThreads = 256;
+constexpr int kWarps = kBuildThreads / 32;
+
+struct BuildArgs {
+  int Lx, Ly, chi, P;
+  double beta;
+  const double* Jh;
+  const double* Jv;
+  const double* h;
+  double* M64;
+  int32_t* bond;
+  double* log_scale;
+  double* sv;
+  double* disc;
+  double* logZ;
+  double* work;   // (Lx + 2) slots of 8 P^2 doubles
+  int32_t* status;
+};
+
+__device__ inline double spin_of(int idx) { return idx ? 1.0 : -1.0; }
+
+__device__ inline double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ inline double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__device__ inline int bond_dim_dev(int chi, int Lx, int Ly, int r, int c) {
+  if (c <= 0 || c >= Lx) return 1;
+  int e = min(min(c, Lx - c), min(Ly - r, 30));
+  return min(chi, 1 << e);
+}
+
+struct Shared {
+  double* W;     // work area
+  int* slot;     // [Lx + 2]
+  int* dl;       // [Lx + 1]
+  int* dr;       // [Lx + 1]
+  int* sel;      // [2P]
+  double* red;   // [64] block reduction scratch
+  int* flag;     // [4]
+};
+
+// Block-wide max of v (all threads must call).
+__device__ double block_max(double v, double* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  v = warp_max(v);
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double r = red[0];
+  for (int i = 1; i < kWarps; ++i) r = fmax(r, red[i]);
+  __syncthreads();
+  return r;
+}
+__device__ double block_sum(double v, double* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  for (int i = 0; i < kWarps; ++i) r += red[i];
+  __syncthreads();
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// 1. MPO application of row r into slots 0..Lx-1.
+// ---------------------------------------------------------------------------
+__device__ void apply_row_mpo(const BuildArgs& a, Shared& sh, int r) {
+  const int Lx = a.Lx, P = a.P;
+  const size_t slot_sz = (size_t)8 * P * P;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int c = w; c < Lx; c += kWarps) {
+    const bool last_row = (r == a.Ly - 1);
+    const int Dl0 = last_row ? 1 : a.bond[(r + 1) * (Lx + 1) + c];
+    const int Dr0 = last_row ? 1 : a.bond[(r + 1) * (Lx + 1) + c + 1];
+    const int kl = (c > 0) ? 2 : 1, kr = (c < Lx - 1) ? 2 : 1;
+    const int Dl = Dl0 * kl, Dr = Dr0 * kr;
+    const double hv = a.h[r * Lx + c];
+    const double hp = exp(a.beta * hv), hm = exp(-a.beta * hv);
+    double vs = 1.0, vd = 1.0, gs = 1.0, gd = 1.0;
+    if (!last_row) {
+      const double jv = a.Jv[r * Lx + c];
+      vs = exp(a.beta * jv);
+      vd = exp(-a.beta * jv);
+    }
+    if (c > 0) {
+      const double jh = a.Jh[r * (Lx - 1) + c - 1];
+      gs = exp(a.beta * jh);
+      gd = exp(-a.beta * jh);
+    }
+    const double* Mn = last_row ? nullptr : a.M64 + ((size_t)(r + 1) * Lx + c) * P * 2 * P;
+    double* out = a.work + (size_t)c * slot_sz;
+    const int total = Dl * 2 * Dr;
+    for (int idx = lane; idx < total; idx += 32) {
+      const int rr = idx % Dr;
+      const int s = (idx / Dr) & 1;
+      const int l = idx / (2 * Dr);
+      int aa = l, k = 0, b = rr, kp = 0;
+      if (kl == 2) { aa = l >> 1; k = l & 1; }
+      if (kr == 2) { b = rr >> 1; kp = rr & 1; }
+      double val = 0.0;
+      if (kr == 1 || kp == s) {
+        double n;
+        if (last_row) {
+          n = 1.0;
+        } else {
+          // sum over the spin s' of row r+1: W[s][s'] = exp(beta Jv s s')
+          const double m0 = Mn[((size_t)aa * 2 + 0) * P + b];
+          const double m1 = Mn[((size_t)aa * 2 + 1) * P + b];
+          n = s ? (vd * m0 + vs * m1) : (vs * m0 + vd * m1);
+        }
+        val = n * (s ? hp : hm);
+        if (kl == 2) val *= (k == s) ? gs : gd;
+      }
+      out[idx] = val;
+    }
+    if (lane == 0) {
+      sh.dl[c] = Dl;
+      sh.dr[c] = Dr;
+      sh.slot[c] = c;
+    }
+  }
+  if (threadIdx.x == 0) {
+    sh.slot[Lx] = Lx;
+    sh.slot[Lx + 1] = Lx + 1;
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Householder QR of a column-major m x n matrix A (lda = m) in shared memory.
+// On exit: R (k x n, k = min(m, n)) in Rout (row-major, ld n), Q (m x k) in Q
+// (column-major, ld m).  Reflector j is stored in A[j*m + j .. ], tau[j].
+// ---------------------------------------------------------------------------
+__device__ void householder_qr(double* A, int m, int n, double* Q, double* Rout, double* tau,
+                               double* diag) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int k = min(m, n);
+  for (int j = 0; j < k; ++j) {
+    if (w == 0) {
+      double s = 0.0;
+      for (int i = j + lane; i < m; i += 32) s += A[j * m + i] * A[j * m + i];
+      s = warp_sum(s);
+      if (lane == 0) {
+        const double x0 = A[j * m + j];
+        const double nrm = sqrt(s);
+        if (nrm == 0.0) {
+          tau[j] = 0.0;
+          diag[j] = 0.0;
+        } else {
+          const double alpha = (x0 > 0.0) ? -nrm : nrm;
+          const double v0 = x0 - alpha;
+          A[j * m + j] = v0;
+          tau[j] = -1.0 / (alpha * v0);
+          diag[j] = alpha;
+        }
+      }
+    }
+    __syncthreads();
+    const double t = tau[j];
+    if (t != 0.0) {
+      for (int l = j + 1 + w; l < n; l += kWarps) {
+        double d = 0.0;
+        for (int i = j + lane; i < m; i += 32) d += A[j * m + i] * A[l * m + i];
+        d = warp_sum(d) * t;
+        for (int i = j + lane; i < m; i += 32) A[l * m + i] -= d * A[j * m + i];
+      }
+    }
+    __syncthreads();
+  }
+  // R
+  for (int idx = threadIdx.x; idx < k * n; idx += blockDim.x) {
+    const int j = idx / n, l = idx % n;
+    Rout[idx] = (l < j) ? 0.0 : (l == j ? diag[j] : A[l * m + j]);
+  }
+  // Q = H_0 ... H_{k-1} [I_k; 0]
+  for (int idx = threadIdx.x; idx < m * k; idx += blockDim.x) {
+    const int l = idx / m, i = idx % m;
+    Q[idx] = (i == l) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  for (int j = k - 1; j >= 0; --j) {
+    const double t = tau[j];
+    if (t != 0.0) {
+      for (int l = j + w; l < k; l += kWarps) {
+        double d = 0.0;
+        for (int i = j + lane; i < m; i += 32) d += A[j * m + i] * Q[l * m + i];
+        d = warp_sum(d) * t;
+        for (int i = j + lane; i < m; i += 32) Q[l * m + i] -= d * A[j * m + i];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 2. Left-to-right QR sweep.  Returns the accumulated log of removed scales.
+// ---------------------------------------------------------------------------
+__device__ double qr_sweep(const BuildArgs& a, Shared& sh) {
+  const int Lx = a.Lx, P = a.P;
+  const size_t slot_sz = (size_t)8 * P * P;
+  double logs = 0.0;
+  double* A = sh.W;
+  double* Q = sh.W + 2 * P * P;
+  double* Rb = sh.W + 4 * P * P;   // R_0 at Rb, R_1 at Rb + P*P
+  double* tau = sh.W + 6 * P * P;
+  double* diag = tau + P;
+  for (int c = 0; c < Lx - 1; ++c) {
+    const int m = sh.dl[c];
+    const int Dr = sh.dr[c];
+    const int nb = Dr / 2;
+    const int k = min(m, nb);
+    const double* X = a.work + (size_t)sh.slot[c] * slot_sz;
+    double* Tn = a.work + (size_t)sh.slot[Lx] * slot_sz;   // new site c: [m][2][2k]
+    for (int sp = 0; sp < 2; ++sp) {
+      for (int idx = threadIdx.x; idx < m * nb; idx += blockDim.x) {
+        const int l = idx / m, i = idx % m;   // column-major A[l*m + i]
+        A[idx] = X[((size_t)i * 2 + sp) * Dr + l * 2 + sp];
+      }
+      __syncthreads();
+      householder_qr(A, m, nb, Q, Rb + sp * P * P, tau, diag);
+      __syncthreads();
+      // new tensor entries (i, s, (j, s')) with s == s' == sp
+      for (int idx = threadIdx.x; idx < m * k; idx += blockDim.x) {
+        const int j = idx / m, i = idx % m;
+        Tn[((size_t)i * 2 + sp) * (2 * k) + j * 2 + sp] = Q[j * m + i];
+        Tn[((size_t)i * 2 + sp) * (2 * k) + j * 2 + (1 - sp)] = 0.0;
+      }
+      __syncthreads();
+    }
+    // scale of R
+    double mx = 0.0;
+    for (int idx = threadIdx.x; idx < k * nb; idx += blockDim.x)
+      mx = fmax(mx, fmax(fabs(Rb[idx]), fabs(Rb[P * P + idx])));
+    mx = block_max(mx, sh.red);
+    if (!(mx > 0.0) || !isfinite(mx)) {
+      if (threadIdx.x == 0) set_status(a.status, TNMC_E_NUMERIC);
+      mx = 1.0;
+    }
+    logs += log(mx);
+    const double inv = 1.0 / mx;
+    // absorb R into site c+1: new[(j,k')][x'] = sum_b R_k'[j][b] old[(b,k')][x']
+    const double* O = a.work + (size_t)sh.slot[c + 1] * slot_sz;
+    double* Nn = a.work + (size_t)sh.slot[Lx + 1] * slot_sz;
+    const int ncol = 2 * sh.dr[c + 1];
+    for (int idx = threadIdx.x; idx < 2 * k * ncol; idx += blockDim.x) {
+      const int row = idx / ncol, col = idx % ncol;
+      const int j = row >> 1, kp = row & 1;
+      const double* Rk = Rb + kp * P * P + j * nb;
+      double acc = 0.0;
+      for (int b = j; b < nb; ++b) acc += Rk[b] * O[((size_t)b * 2 + kp) * ncol + col];
+      Nn[idx] = acc * inv;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int t = sh.slot[c];
+      sh.slot[c] = sh.slot[Lx];
+      sh.slot[Lx] = t;
+      t = sh.slot[c + 1];
+      sh.slot[c + 1] = sh.slot[Lx + 1];
+      sh.slot[Lx + 1] = t;
+      sh.dr[c] = 2 * k;
+      sh.dl[c + 1] = 2 * k;
+    }
+    __syncthreads();
+  }
+  return logs;
+}
+
+// Round-robin tournament: round t of N-1 (N even), pair i of N/2.
+__device__ inline void tournament(int t, int i, int N, int& p, int& q) {
+  if (i == 0) {
+    p = N - 1;
+    q = t;
+  } else {
+    p = (t + i) % (N - 1);
+    q = (t - i + (N - 1)) % (N - 1);
+  }
+}
+
+// One-sided Jacobi: orthogonalise the m rows (length n, stride ld) of J.
+__device__ void jacobi_rows(double* J, int m, int n, int ld, int* flag) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int N = m + (m & 1);
+  const double tol = 1e-15;
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    if (threadIdx.x == 0) flag[0] = 0;
+    __syncthreads();
+    for (int t = 0; t < N - 1; ++t) {
+      for (int i = w; i < N / 2; i += kWarps) {
+        int p, q;
+        tournament(t, i, N, p, q);
+        if (p >= m || q >= m) continue;
+        double* rp = J + (size_t)p * ld;
+        double* rq = J + (size_t)q * ld;
+        double al = 0.0, be = 0.0, ga = 0.0;
+        for (int x = lane; x < n; x += 32) {
+          const double u = rp[x], v = rq[x];
+          al += u * u;
+          be += v * v;
+          ga += u * v;
+        }
+        al = warp_sum(al);
+        be = warp_sum(be);
+        ga = warp_sum(ga);
+        if (ga != 0.0 && fabs(ga) > tol * sqrt(al * be)) {
+          const double zeta = (be - al) / (2.0 * ga);
+          double tt;
+          if (fabs(zeta) > 1e150)
+            tt = 0.5 / zeta;
+          else
+            tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          const double cs = 1.0 / sqrt(1.0 + tt * tt);
+          const double sn = cs * tt;
+          for (int x = lane; x < n; x += 32) {
+            const double u = rp[x], v = rq[x];
+            rp[x] = cs * u - sn * v;
+            rq[x] = sn * u + cs * v;
+          }
+          if (lane == 0) flag[0] = 1;
+        }
+      }
+      __syncthreads();
+    }
+    const int rotated = flag[0];
+    __syncthreads();
+    if (!rotated) break;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 3. Right-to-left SVD sweep with truncation.
+// ---------------------------------------------------------------------------
+__device__ double svd_sweep(const BuildArgs& a, Shared& sh, int r) {
+  const int Lx = a.Lx, P = a.P;
+  const size_t slot_sz = (size_t)8 * P * P;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  double logs = 0.0;
+  for (int c = Lx - 1; c >= 1; --c) {
+    const int m = sh.dl[c];
+    const int n = 2 * sh.dr[c];
+    const int ld = n + 1;
+    double* J = sh.W;
+    double* US = sh.W + 4 * P * P + 2 * P;
+    double* nrm = sh.W + 6 * P * P + 2 * P;
+    const double* A = a.work + (size_t)sh.slot[c] * slot_sz;
+    const int kk = bond_dim_dev(a.chi, Lx, a.Ly, r, c);
+    if (kk > min(m, n)) {
+      if (threadIdx.x == 0) set_status(a.status, TNMC_E_NUMERIC);
+      return logs;
+    }
+    for (int idx = threadIdx.x; idx < m * n; idx += blockDim.x) J[(idx / n) * ld + idx % n] = A[idx];
+    __syncthreads();
+    jacobi_rows(J, m, n, ld, sh.flag);
+    for (int i = w; i < m; i += kWarps) {
+      double s = 0.0;
+      for (int x = lane; x < n; x += 32) s += J[i * ld + x] * J[i * ld + x];
+      s = warp_sum(s);
+      if (lane == 0) nrm[i] = sqrt(s);
+    }
+    __syncthreads();
+    // rank of each row by norm (descending; ties by index) -> sel[rank] = row
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      int rank = 0;
+      const double ni = nrm[i];
+      for (int j = 0; j < m; ++j) {
+        const double nj = nrm[j];
+        rank += (nj > ni) || (nj == ni && j < i);
+      }
+      if (rank < kk) sh.sel[rank] = i;
+    }
+    __syncthreads();
+    // singular-value record
+    double tot = 0.0, dsc = 0.0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) tot += nrm[i] * nrm[i];
+    tot = block_sum(tot, sh.red);
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+      // rows not selected
+      int rank = 0;
+      for (int i = 0; i < m; ++i) rank += (nrm[i] > nrm[j]) || (nrm[i] == nrm[j] && i < j);
+      if (rank >= kk) dsc += nrm[j] * nrm[j];
+    }
+    dsc = block_sum(dsc, sh.red);
+    const double smax = nrm[sh.sel[0]];
+    if (!(smax > 0.0) || !isfinite(smax)) {
+      if (threadIdx.x == 0) set_status(a.status, TNMC_E_NUMERIC);
+      return logs;
+    }
+    double* svr = a.sv + ((size_t)r * (Lx + 1) + c) * P;
+    for (int j = threadIdx.x; j < P; j += blockDim.x) svr[j] = (j < kk) ? nrm[sh.sel[j]] / sqrt(tot) : 0.0;
+    if (threadIdx.x == 0) a.disc[r * (Lx + 1) + c] = dsc / tot;
+    // V_k^T rows into the spare slot: new site c, [kk][2][dr]
+    double* Vt = a.work + (size_t)sh.slot[Lx] * slot_sz;
+    for (int idx = threadIdx.x; idx < kk * n; idx += blockDim.x) {
+      const int j = idx / n, x = idx % n;
+      const int i = sh.sel[j];
+      const double nv = nrm[i];
+      Vt[idx] = (nv > 1e-280) ? J[i * ld + x] / nv : 0.0;
+    }
+    __syncthreads();
+    // orthonormal completion for (numerically) zero rows -- rare, one warp
+    if (w == 0) {
+      for (int j = 0; j < kk; ++j) {
+        if (nrm[sh.sel[j]] > 1e-280) continue;
+        for (int e = 0; e < n; ++e) {
+          for (int x = lane; x < n; x += 32) Vt[j * n + x] = (x == e) ? 1.0 : 0.0;
+          __syncwarp();
+          for (int pass = 0; pass < 2; ++pass) {
+            for (int i = 0; i < kk; ++i) {
+              if (i == j) continue;
+              if (nrm[sh.sel[i]] <= 1e-280 && i > j) continue;
+              double d = 0.0;
+              for (int x = lane; x < n; x += 32) d += Vt[i * n + x] * Vt[j * n + x];
+              d = warp_sum(d);
+              for (int x = lane; x < n; x += 32) Vt[j * n + x] -= d * Vt[i * n + x];
+              __syncwarp();
+            }
+          }
+          double s = 0.0;
+          for (int x = lane; x < n; x += 32) s += Vt[j * n + x] * Vt[j * n + x];
+          s = sqrt(warp_sum(s));
+          if (s > 0.5) {
+            for (int x = lane; x < n; x += 32) Vt[j * n + x] /= s;
+            __syncwarp();
+            break;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    // US = A V_k / smax  (m x kk), A from the original slot
+    const double inv = 1.0 / smax;
+    for (int idx = threadIdx.x; idx < m * kk; idx += blockDim.x) {
+      const int i = idx / kk, j = idx % kk;
+      double acc = 0.0;
+      for (int x = 0; x < n; ++x) acc += A[(size_t)i * n + x] * Vt[(size_t)j * n + x];
+      US[idx] = acc * inv;
+    }
+    __syncthreads();
+    logs += log(smax);
+    // absorb into site c-1: rows (l, s) of length m -> length kk
+    const double* O = a.work + (size_t)sh.slot[c - 1] * slot_sz;
+    double* Nn = a.work + (size_t)sh.slot[Lx + 1] * slot_sz;
+    const int rows = sh.dl[c - 1] * 2;
+    for (int idx = threadIdx.x; idx < rows * kk; idx += blockDim.x) {
+      const int q = idx / kk, j = idx % kk;
+      double acc = 0.0;
+      for (int i = 0; i < m; ++i) acc += O[(size_t)q * m + i] * US[i * kk + j];
+      Nn[idx] = acc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int t = sh.slot[c];
+      sh.slot[c] = sh.slot[Lx];
+      sh.slot[Lx] = t;
+      t = sh.slot[c - 1];
+      sh.slot[c - 1] = sh.slot[Lx + 1];
+      sh.slot[Lx + 1] = t;
+      sh.dl[c] = kk;
+      sh.dr[c - 1] = kk;
+    }
+    __syncthreads();
+  }
+  return logs;
+}
+
+__global__ void __launch_bounds__(kBuildThreads) build_env_kernel(BuildArgs a) {
+  extern __shared__ double smem[];
+  const int Lx = a.Lx, P = a.P;
+  Shared sh;
+  sh.W = smem;
+  sh.red = smem + 6 * P * P + 4 * P;
+  int* ip = reinterpret_cast<int*>(sh.red + 64);
+  sh.slot = ip;
+  sh.dl = ip + (Lx + 2);
+  sh.dr = sh.dl + (Lx + 1);
+  sh.sel = sh.dr + (Lx + 1);
+  sh.flag = sh.sel + 2 * P;
+  const size_t slot_sz = (size_t)8 * P * P;
+
+  for (int r = a.Ly - 1; r >= 0; --r) {
+    apply_row_mpo(a, sh, r);
+    double logs = qr_sweep(a, sh);
+    logs += svd_sweep(a, sh, r);
+    // normalise site 0
+    {
+      const double* T0 = a.work + (size_t)sh.slot[0] * slot_sz;
+      const int cnt = sh.dl[0] * 2 * sh.dr[0];
+      double s = 0.0;
+      for (int idx = threadIdx.x; idx < cnt; idx += blockDim.x) s += T0[idx] * T0[idx];
+      s = block_sum(s, sh.red);
+      const double n0 = sqrt(s);
+      if (!(n0 > 0.0) || !isfinite(n0)) {
+        if (threadIdx.x == 0) set_status(a.status, TNMC_E_NUMERIC);
+      }
+      logs += log(n0);
+      // write the row into the padded FP64 arena
+      for (int c = 0; c < Lx; ++c) {
+        const int Dl = sh.dl[c], Dr = sh.dr[c];
+        const double* T = a.work + (size_t)sh.slot[c] * slot_sz;
+        double* out = a.M64 + ((size_t)r * Lx + c) * P * 2 * P;
+        const double scale = (c == 0) ? 1.0 / n0 : 1.0;
+        for (int idx = threadIdx.x; idx < P * 2 * P; idx += blockDim.x) {
+          const int b = idx % P, s2 = (idx / P) & 1, aa = idx / (2 * P);
+          out[idx] = (aa < Dl && b < Dr) ? T[((size_t)aa * 2 + s2) * Dr + b] * scale : 0.0;
+        }
+        if (threadIdx.x == 0) {
+          a.bond[r * (Lx + 1) + c] = Dl;
+          if (Dl != bond_dim_dev(a.chi, Lx, a.Ly, r, c)) set_status(a.status, TNMC_E_NUMERIC);
+        }
+      }
+      if (threadIdx.x == 0) {
+        a.bond[r * (Lx + 1) + Lx] = 1;
+        a.log_scale[r] = logs;
+      }
+    }
+    __syncthreads();
+  }
+  // log Z~ = sum_r log_scale[r] + log sum_sigma env_0(sigma)  (row 0 has no field from above)
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    double* v = sh.W;          // [P]
+    double* v2 = sh.W + P;     // [P]
+    for (int i = lane; i < P; i += 32) v[i] = (i == 0) ? 1.0 : 0.0;
+    __syncwarp();
+    double logv = 0.0;
+    for (int c = 0; c < Lx; ++c) {
+      const double* M = a.M64 + (size_t)c * P * 2 * P;
+      const int Dl = a.bond[c], Dr = a.bond[c + 1];
+      double mx = 0.0;
+      for (int b = lane; b < Dr; b += 32) {
+        double acc = 0.0;
+        for (int aa = 0; aa < Dl; ++aa) acc += v[aa] * (M[((size_t)aa * 2) * P + b] + M[((size_t)aa * 2 + 1) * P + b]);
+        v2[b] = acc;
+        mx = fmax(mx, fabs(acc));
+      }
+      mx = warp_max(mx);
+      __syncwarp();
+      for (int b = lane; b < P; b += 32) v[b] = (b < Dr && mx > 0.0) ? v2[b] / mx : 0.0;
+      if (mx > 0.0) logv += log(mx);
+      __syncwarp();
+    }
+    if (lane == 0) {
+      double tot = 0.0;
+      for (int r = 0; r < a.Ly; ++r) tot += a.log_scale[r];
+      *a.logZ = (v[0] > 0.0) ? tot + logv + log(v[0]) : NAN;
+    }
+  }
+}
+
+}  // namespace
+}  // namespace tnmc
+
+size_t tnmc_build_work_bytes(int Lx, int Ly, int P) {
+  (void)Ly;
+  return (size_t)(Lx + 2) * 8 * P * P * sizeof(double);
+}
+
+static size_t build_smem_bytes(int Lx, int P) {
+  return (size_t)(6 * P * P + 4 * P + 64) * sizeof(double) + (size_t)(3 * Lx + 4 + 2 * P + 8) * sizeof(int);
+}
+
+tnmc_status tnmc_launch_build(tnmc_env* env, cudaStream_t stream, void* work, size_t work_bytes) {
+  using namespace tnmc;
+  const DeviceEnv& d = env->d;
+  if (work_bytes < tnmc_build_work_bytes(d.Lx, d.Ly, d.P)) {
+    tnmc_set_error("build scratch too small");
+    return TNMC_E_INVALID_ARG;
+  }
+  BuildArgs a;
+  a.Lx = d.Lx;
+  a.Ly = d.Ly;
+  a.chi = d.chi;
+  a.P = d.P;
+  a.beta = d.beta;
+  a.Jh = d.Jh;
+  a.Jv = d.Jv;
+  a.h = d.h;
+  a.M64 = const_cast<double*>(d.M64);
+  a.bond = const_cast<int32_t*>(d.bond);
+  a.log_scale = env->log_scale;
+  a.sv = env->sv;
+  a.disc = env->discarded;
+  a.logZ = env->logZ;
+  a.work = static_cast<double*>(work);
+  a.status = d.status;
+  const size_t smem = build_smem_bytes(d.Lx, d.P);
+  int dev = 0, max_optin = 0;
+  TNMC_CUDA_TRY(cudaGetDevice(&dev));
+  TNMC_CUDA_TRY(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  if (smem > (size_t)max_optin) {
+    tnmc_set_error("builder needs %zu bytes of shared memory (device allows %d): Lx too large", smem, max_optin);
+    return TNMC_E_UNSUPPORTED;
+  }
+  TNMC_CUDA_TRY(cudaFuncSetAttribute(build_env_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  build_env_kernel<<<1, kBuildThreads, smem, stream>>>(a);
+  TNMC_CUDA_TRY(cudaGetLastError());
+  return TNMC_OK;
+}

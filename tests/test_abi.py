@@ -1,0 +1,65 @@
+"""The C-ABI library builds, loads and exports every symbol include/tnmc.h declares (no GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", f)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(tnmc_[a-z0-9_]+)\s*\(", txt))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_2104_13264_gb300 import binding, build
+    if not os.path.exists(binding.LIB_PATH):
+        build.build()
+    return binding.LIB_PATH
+
+
+def test_header_declares_entry_points():
+    names = declared_symbols()
+    for required in ("tnmc_build_env", "tnmc_sample", "tnmc_logq", "tnmc_mh_step", "tnmc_init_chains",
+                     "tnmc_env_free", "tnmc_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    for name in declared_symbols():
+        assert hasattr(lib, name), name
+
+
+def test_binding_signatures_cover_header():
+    from paper_2104_13264_gb300 import binding
+    assert set(declared_symbols()) <= set(binding.SIGNATURES)
+
+
+def test_argument_errors_reported_without_gpu(libpath):
+    """Argument checks run before any CUDA call, so they work on a machine without a GPU."""
+    from paper_2104_13264_gb300 import binding
+    L = binding.lib()
+    out = ctypes.c_void_p()
+    st = L.tnmc_build_env(None, 1.0, 4, 0, None, ctypes.byref(out))
+    assert st == 1
+    assert b"non-null" in L.tnmc_last_error()
+    import numpy as np
+    h = np.zeros((2, 2))
+    J = np.ones((2, 1))
+    lat = binding._Lattice(2, 2, J.ctypes.data, J.ctypes.data, h.ctypes.data)
+    assert L.tnmc_build_env(ctypes.byref(lat), 1.0, 0, 0, None, ctypes.byref(out)) == 1
+    assert L.tnmc_build_env(ctypes.byref(lat), 1.0, 65, 0, None, ctypes.byref(out)) == 1
+    assert L.tnmc_build_env(ctypes.byref(lat), float("nan"), 4, 0, None, ctypes.byref(out)) == 1
+    hb = np.array([[0.0, float("inf")], [0.0, 0.0]])
+    lat2 = binding._Lattice(2, 2, J.ctypes.data, J.ctypes.data, hb.ctypes.data)
+    assert L.tnmc_build_env(ctypes.byref(lat2), 1.0, 4, 0, None, ctypes.byref(out)) == 1
+    assert b"not finite" in L.tnmc_last_error()
