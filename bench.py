@@ -1,0 +1,431 @@
+"""Benchmark of the TNMH proposal path: accepted samples/s (and proposals/s).
+
+One step = draw B proposals (tnmc_sample) + the MH scan of C chains over them
+(tnmc_mh_step), on an environment built beforehand (the build is amortised
+over the chain and reported separately as env_build_s).  Inputs are synthetic
+instances from paper_2104_13264_gb300.instances.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--config c5] [--precision bf16]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on a bounded sample
+
+N > 1 (torchrun): independent replicas, rank i draws sample indices
+[i B, (i+1) B); no collective on the data path; timing is the max over ranks.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+CONFIGS = {
+    # name: (instance factory, B, chains C, default precision, description)
+    "c1": ("config1", 10000, 1, "f64", "8x8 ferromagnet, beta=0.44, chi=8, 10^4 proposals, 1 chain"),
+    "c2": ("config2", 65536, 256, "f32", "32x32 +-J EA, beta=1.0, chi=16, B=65536"),
+    "c4": ("config4", 16384, 64, "f32", "64x64 fully frustrated, beta=1.5, chi=32, B=16384"),
+    "c5": ("config5", 1 << 20, 1024, "bf16", "256x256 ferromagnet, beta=0.4407, chi=64, B=2^20"),
+}
+
+
+def algorithmic_flops(inst):
+    """8 chi_c chi_{c+1} FLOP per site per sample for rows r >= 1, 4 chi chi' for row 0
+    (its right sweep does not depend on the sample): the left and right sweeps."""
+    from paper_2104_13264_gb300.instances import Instance  # noqa: F401
+    Lx, Ly, chi = inst.Lx, inst.Ly, inst.chi
+
+    def bd(r, c):
+        if c <= 0 or c >= Lx:
+            return 1
+        return min(chi, 1 << min(c, Lx - c, Ly - r, 30))
+
+    tot = 0
+    for r in range(Ly):
+        for c in range(Lx):
+            tot += (8 if r > 0 else 4) * bd(r, c) * bd(r, c + 1)
+    return tot
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_tnmc(args):
+    import torch
+    from paper_2104_13264_gb300 import binding as Bd
+    from paper_2104_13264_gb300 import instances
+
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+    fac, Bdef, Cdef, pdef, desc = CONFIGS[args.config]
+    inst = getattr(instances, fac)()
+    B = args.batch or Bdef
+    C = args.chains or Cdef
+    assert B % C == 0
+    T = B // C
+    prec = args.precision or pdef
+    dev = torch.device("cuda", local)
+
+    t0 = time.time()
+    env = Bd.Env.from_instance(inst, precisions=tuple(sorted({"f64", prec})))
+    info = env.info()
+    env_build_s = time.time() - t0
+
+    spins = torch.empty((B, inst.Ly, inst.Lx), dtype=torch.int8, device=dev)
+    logq = torch.empty(B, dtype=torch.float64, device=dev)
+    energy = torch.empty(B, dtype=torch.float64, device=dev)
+    flags = torch.empty(B, dtype=torch.int32, device=dev)
+    acc = torch.empty(B, dtype=torch.uint8, device=dev)
+    nacc = torch.zeros(1, dtype=torch.int64, device=dev)
+    chain = Bd.init_chains(env, C, seed=args.seed + 7919 * rank, precision=prec)
+    stream = torch.cuda.current_stream()
+    l2_bytes = 126 * (1 << 20)
+    out_bytes = spins.numel()
+    flush = None if out_bytes > 2 * l2_bytes else torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev_m = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+
+    def step(i, timed):
+        off = (rank * B) + (i * B * world)
+        if flush is not None:
+            flush.fill_(i & 0xFF)
+        if timed:
+            ev_s[i].record(stream)
+        Bd.sample(env, B, seed=args.seed, sample_offset=off, precision=prec,
+                  out=(spins, logq, energy, flags), stream=stream)
+        if timed:
+            ev_m[i].record(stream)
+        Bd.mh_step(env, C, T, (spins, logq, energy), chain, seed=args.seed + 1, step_offset=i * T,
+                   accepted=acc, n_accepted=nacc, stream=stream)
+        if timed:
+            ev_e[i].record(stream)
+
+    for i in range(args.warmup):
+        step(i, False)
+    torch.cuda.synchronize()
+    nacc.zero_()
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    wall0 = time.time()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for i in range(args.steps):
+        step(i, True)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    wall = time.time() - wall0
+    clk = clocks.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    sample_ms = [ev_s[i].elapsed_time(ev_m[i]) for i in range(args.steps)]
+    n_accepted = int(nacc.item())
+    if pg:
+        t = torch.tensor([total_ms, float(n_accepted)], dtype=torch.float64, device=dev)
+        mx = t.clone()
+        pg.all_reduce(mx, op=pg.ReduceOp.MAX)
+        sm = t.clone()
+        pg.all_reduce(sm, op=pg.ReduceOp.SUM)
+        total_ms = float(mx[0])
+        n_accepted = int(sm[1])
+    status = env.status()
+
+    # end-to-end through the public API with host buffers: chain states live in pinned
+    # host memory; every step uploads them, samples, runs MH, and reads back the chain
+    # states and the accept flags.
+    hs = torch.empty((C, inst.Ly, inst.Lx), dtype=torch.int8, pin_memory=True)
+    hlq = torch.empty(C, dtype=torch.float64, pin_memory=True)
+    hE = torch.empty(C, dtype=torch.float64, pin_memory=True)
+    hacc = torch.empty(B, dtype=torch.uint8, pin_memory=True)
+    hs.copy_(chain[0].cpu()); hlq.copy_(chain[1].cpu()); hE.copy_(chain[2].cpu())
+    dchain = (torch.empty_like(chain[0]), torch.empty_like(chain[1]), torch.empty_like(chain[2]))
+    nacc_e = torch.zeros(1, dtype=torch.int64, device=dev)
+    e2e_steps = max(1, min(args.steps, 3))
+    h2d = hs.numel() + 16 * C
+    d2h = hs.numel() + 16 * C + B
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(e2e_steps):
+        off = (rank * B) + ((args.steps + i) * B * world)
+        dchain[0].copy_(hs, non_blocking=True); dchain[1].copy_(hlq, non_blocking=True); dchain[2].copy_(hE, non_blocking=True)
+        Bd.sample(env, B, seed=args.seed, sample_offset=off, precision=prec, out=(spins, logq, energy, flags), stream=stream)
+        Bd.mh_step(env, C, T, (spins, logq, energy), dchain, seed=args.seed + 1, step_offset=(args.steps + i) * T,
+                   accepted=acc, n_accepted=nacc_e, stream=stream)
+        hs.copy_(dchain[0], non_blocking=True); hlq.copy_(dchain[1], non_blocking=True); hE.copy_(dchain[2], non_blocking=True)
+        hacc.copy_(acc, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    e2e_acc = int(nacc_e.item())
+
+    if rank != 0:
+        if pg:
+            pg.destroy_process_group()
+        return
+    peaks, peak_src = load_peaks()
+    flops = algorithmic_flops(inst)
+    kern_s = statistics.mean(sample_ms) / 1e3
+    achieved_tf = flops * B / kern_s / 1e12
+    smmax = float(peaks.get("sm_max_mhz", 2070.0))
+    if prec == "bf16":
+        peak = float(peaks["bf16_tflops_sustained"])
+        roof = {"bound": "tensor", "unit": "TFLOP/s", "peak_source": peak_src + " bf16_tflops_sustained"}
+    elif prec == "f32":
+        peak = 152 * 128 * 2 * smmax * 1e6 / 1e12
+        roof = {"bound": "alu", "unit": "TFLOP/s", "peak_source": "FP32 FFMA: 152 SM x 128 lanes x 2 x %.0f MHz" % smmax}
+    else:
+        peak = 1.25
+        roof = {"bound": "alu", "unit": "TFLOP/s", "peak_source": "FP64 nominal 1.25 TFLOP/s"}
+    roof.update({"achieved": round(achieved_tf, 3), "peak": round(peak, 3), "frac": round(achieved_tf / peak, 5),
+                 "traffic": None, "kernel": "sample_%s" % prec, "flop_per_sample": flops})
+    step_ms = total_ms / args.steps
+    props_s = B * world / (step_ms / 1e3)
+    acc_rate = n_accepted / (B * world * args.steps)
+    value = n_accepted / (total_ms / 1e3)
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.config, prec, args.cpu_seconds)
+        if cpu is not None:
+            cpu["value"] = cpu["value"] * acc_rate       # accepted/s at the same acceptance
+            cpu["unit"] = "accepted samples/s"
+    line = {
+        "metric": "accepted samples/s (TNMH proposals + MH, %s)" % desc,
+        "value": round(value, 3), "unit": "accepted samples/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(step_ms, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": {"f64": "f64", "f32": "f32", "bf16": "bf16"}[prec],
+        "data": "synthetic (seeded instance generator)",
+        "config": {"workload": args.config, "description": desc, "Lx": inst.Lx, "Ly": inst.Ly, "chi": inst.chi,
+                   "beta": inst.beta, "B": B, "chains": C, "proposals_per_chain": T, "precision": prec,
+                   "parallelism": "replicas%d" % world,
+                   "l2": "flushed (256 MiB write between steps)" if flush is not None else "outputs > L2"},
+        "proposals_per_s": round(props_s, 3), "acceptance": round(acc_rate, 5),
+        "env_build_s": round(env_build_s, 3), "logZ": info["logZ"], "device_status": status,
+        "roofline": roof, "cpu_baseline": cpu,
+        "e2e": {"value": round(e2e_acc / (e2e_ms * e2e_steps / 1e3), 3) if e2e_ms > 0 else None,
+                "unit": "accepted samples/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "ms_per_step": round(e2e_ms, 3)},
+        "gpu_launches": 3 * args.steps,
+        "clocks": clk, "wall_s": round(wall, 3),
+    }
+    print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+
+
+def _oracle_workload(config, n_rows_cap):
+    """Oracle environment for timing: the real one when cheap, else random tensors with
+    the configuration's bond dimensions for the first rows (the oracle's cost does not
+    depend on the tensor values)."""
+    import numpy as np
+
+    from oracle import tnmc
+    from paper_2104_13264_gb300 import instances
+    fac = CONFIGS[config][0]
+    inst = getattr(instances, fac)()
+    if inst.Lx * inst.Ly <= 4096:
+        env = tnmc.build_env(inst.Jh, inst.Jv, inst.h, inst.beta, inst.chi)
+        return env, inst, inst.Ly, "oracle-built environment"
+    rows = min(inst.Ly, n_rows_cap)
+    rng = np.random.default_rng(0)
+    env = tnmc.Env(inst.Lx, rows, inst.beta, inst.chi, inst.Jh[:rows], inst.Jv[:rows - 1], inst.h[:rows])
+    for r in range(rows):
+        env.M[r] = [rng.standard_normal((tnmc.bond_dim(inst.chi, inst.Lx, inst.Ly, r, c), 2,
+                                         tnmc.bond_dim(inst.chi, inst.Lx, inst.Ly, r, c + 1))) ** 2
+                    for c in range(inst.Lx)]
+    return env, inst, rows, "random positive tensors with the bond dimensions of the first %d rows" % rows
+
+
+def cpu_baseline(config, prec, seconds):
+    """Time the FP64 oracle on the host cores on a bounded sample; returns proposals/s."""
+    code = ("import sys, json; sys.path.insert(0, %r); import bench; print(json.dumps(bench._cpu_rate(%r, %r)))"
+            % (ROOT, config, float(seconds)))
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    try:
+        p = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=600)
+        return json.loads(p.stdout.strip().splitlines()[-1])
+    except Exception as e:  # noqa: BLE001
+        return {"value": None, "error": str(e)[-200:]}
+
+
+def _cpu_rate(config, seconds):
+    from oracle import tnmc
+    env, inst, rows, how = _oracle_workload(config, 4)
+    nB = 1
+    t = 0.0
+    while True:
+        t0 = time.time()
+        tnmc.sample(env, nB, seed=0)
+        t = time.time() - t0
+        if t > seconds / 4 or nB >= (1 << 16):
+            break
+        nB *= 4
+    per_sample = t / nB * (inst.Ly / rows)
+    return {"value": 1.0 / per_sample, "unit": "proposals/s", "cores": 1, "kind": "oracle",
+            "sample": "%d proposals of %s over %d of %d rows (%s), scaled to the full lattice; numpy, 1 thread"
+                      % (nB, config, rows, inst.Ly, how)}
+
+
+def run_reference(args):
+    """The FP64 oracle timed on the host cores as the reference arm (rank 0 only).
+
+    Each step draws a bounded batch of proposals with the oracle sampler; where the
+    oracle's own environment is affordable (n <= 4096 sites) it also runs the oracle
+    MH scan on them and reports accepted samples/s, otherwise (the 256 x 256 lattice,
+    timed on random tensors of the right shapes) it reports proposals/s.
+    """
+    world, rank, local = dist_setup(args)
+    if rank != 0:
+        return
+    from oracle import tnmc
+    env, inst, rows, how = _oracle_workload(args.config, 4)
+    fac, Bdef, Cdef, pdef, desc = CONFIGS[args.config]
+    real = rows == inst.Ly and how.startswith("oracle")
+    nB = args.cpu_batch
+    if nB <= 0:                       # calibrate: about 2 s of oracle work per step
+        nB = 1
+        while nB < 65536:
+            t0 = time.time()
+            tnmc.sample(env, nB, seed=0)
+            if time.time() - t0 > 0.5:
+                break
+            nB *= 2
+        nB = min(65536, nB * 4)
+    for _ in range(args.warmup):
+        tnmc.sample(env, nB, seed=0)
+    times, acc_n = [], 0
+    C = max(1, nB // 16)
+    T = nB // C
+    for i in range(args.steps):
+        t0 = time.time()
+        sp, lq, E, fl = tnmc.sample(env, C * T, seed=0, sample_offset=i * nB)
+        if real:
+            cs, clq, cE = tnmc.init_chains(env, C, seed=1) if i == 0 else (cs, clq, cE)
+            a, cs, clq, cE = tnmc.mh_scan(inst.beta, C, T, sp, lq, E, cs, clq, cE, seed=1, step_offset=i * T)
+            acc_n += int(a.sum())
+        times.append(time.time() - t0)
+    scale = inst.Ly / rows
+    per_step = statistics.mean(times) * scale
+    if real:
+        value, unit = acc_n / (sum(times) * scale), "accepted samples/s"
+    else:
+        value, unit = C * T / per_step, "proposals/s (oracle timed on random tensors; no acceptance)"
+    cpu = {"value": round(value, 6), "unit": unit, "cores": 1, "kind": "oracle",
+           "sample": "%d proposals per step over %d of %d rows (%s)%s" % (C * T, rows, inst.Ly, how,
+                                                                        ", scaled" if scale != 1 else "")}
+    line = {"impl": "reference", "metric": "accepted samples/s (TNMH proposals + MH, %s)" % desc,
+            "value": round(value, 6), "unit": unit, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(per_step * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded instance generator)",
+            "config": {"workload": args.config, "description": desc, "proposals_per_step": C * T},
+            "cpu_baseline": cpu,
+            "e2e": {"value": round(value, 6), "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="tnmc", choices=["tnmc", "reference"])
+    ap.add_argument("--config", default=os.environ.get("TNMC_BENCH_CONFIG", "c5"), choices=sorted(CONFIGS))
+    ap.add_argument("--precision", default=None, choices=["f64", "f32", "bf16"])
+    ap.add_argument("--batch", type=int, default=None)
+    ap.add_argument("--chains", type=int, default=None)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cpu-batch", type=int, default=0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_tnmc(args)
+
+
+if __name__ == "__main__":
+    main()

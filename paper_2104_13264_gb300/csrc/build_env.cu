@@ -43,7 +43,6 @@ struct BuildArgs {
   int32_t* status;
 };
 
-__device__ inline double spin_of(int idx) { return idx ? 1.0 : -1.0; }
 
 __device__ inline double warp_sum(double v) {
 #pragma unroll
@@ -312,31 +311,38 @@ __device__ inline void tournament(int t, int i, int N, int& p, int& q) {
   }
 }
 
-// One-sided Jacobi: orthogonalise the m rows (length n, stride ld) of J.
-__device__ void jacobi_rows(double* J, int m, int n, int ld, int* flag) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+// One-sided Jacobi (Hestenes): orthogonalise the m <= 128 rows (length n, stride
+// ld) of J.  Round-robin pairing; four lanes own one pair (all m/2 pairs of a
+// round run at once on 256 threads).  Squared row norms d[] are maintained
+// through the exact update alpha' = alpha - t gamma, beta' = beta + t gamma and
+// recomputed at the start of every sweep.  A pair is rotated while
+// |gamma| > tol sqrt(alpha beta); tol = 1e-13 sits above the rounding level of a
+// length-128 dot product, so the sweep count stays small.
+__device__ void jacobi_rows(double* J, int m, int n, int ld, double* d, int* flag) {
+  const int quad = threadIdx.x >> 2, ql = threadIdx.x & 3;
   const int N = m + (m & 1);
-  const double tol = 1e-15;
-  for (int sweep = 0; sweep < 60; ++sweep) {
+  const double tol = 1e-13;
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      double s = 0.0;
+      for (int x = 0; x < n; ++x) s += J[(size_t)i * ld + x] * J[(size_t)i * ld + x];
+      d[i] = s;
+    }
     if (threadIdx.x == 0) flag[0] = 0;
     __syncthreads();
     for (int t = 0; t < N - 1; ++t) {
-      for (int i = w; i < N / 2; i += kWarps) {
-        int p, q;
-        tournament(t, i, N, p, q);
-        if (p >= m || q >= m) continue;
-        double* rp = J + (size_t)p * ld;
-        double* rq = J + (size_t)q * ld;
-        double al = 0.0, be = 0.0, ga = 0.0;
-        for (int x = lane; x < n; x += 32) {
-          const double u = rp[x], v = rq[x];
-          al += u * u;
-          be += v * v;
-          ga += u * v;
-        }
-        al = warp_sum(al);
-        be = warp_sum(be);
-        ga = warp_sum(ga);
+      int p = -1, q = -1;
+      if (quad < N / 2) tournament(t, quad, N, p, q);
+      const bool live = (quad < N / 2) && p < m && q < m;
+      double ga = 0.0;
+      double* rp = J + (size_t)(live ? p : 0) * ld;
+      double* rq = J + (size_t)(live ? q : 0) * ld;
+      if (live)
+        for (int x = ql; x < n; x += 4) ga += rp[x] * rq[x];
+      ga += __shfl_xor_sync(0xffffffffu, ga, 1);
+      ga += __shfl_xor_sync(0xffffffffu, ga, 2);
+      if (live) {
+        const double al = d[p], be = d[q];
         if (ga != 0.0 && fabs(ga) > tol * sqrt(al * be)) {
           const double zeta = (be - al) / (2.0 * ga);
           double tt;
@@ -346,12 +352,16 @@ __device__ void jacobi_rows(double* J, int m, int n, int ld, int* flag) {
             tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
           const double cs = 1.0 / sqrt(1.0 + tt * tt);
           const double sn = cs * tt;
-          for (int x = lane; x < n; x += 32) {
+          for (int x = ql; x < n; x += 4) {
             const double u = rp[x], v = rq[x];
             rp[x] = cs * u - sn * v;
             rq[x] = sn * u + cs * v;
           }
-          if (lane == 0) flag[0] = 1;
+          if (ql == 0) {
+            d[p] = al - tt * ga;
+            d[q] = be + tt * ga;
+            flag[0] = 1;
+          }
         }
       }
       __syncthreads();
@@ -385,7 +395,7 @@ __device__ double svd_sweep(const BuildArgs& a, Shared& sh, int r) {
     }
     for (int idx = threadIdx.x; idx < m * n; idx += blockDim.x) J[(idx / n) * ld + idx % n] = A[idx];
     __syncthreads();
-    jacobi_rows(J, m, n, ld, sh.flag);
+    jacobi_rows(J, m, n, ld, nrm, sh.flag);
     for (int i = w; i < m; i += kWarps) {
       double s = 0.0;
       for (int x = lane; x < n; x += 32) s += J[i * ld + x] * J[i * ld + x];
