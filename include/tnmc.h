@@ -138,6 +138,27 @@ tnmc_status tnmc_sample(const tnmc_env* env, int precision, int64_t B, uint64_t 
                         int32_t* flags, void* stream);
 
 /*
+ * tnmc_sample without any device allocation.  The paper has no counterpart:
+ * this exists for callers that cannot let the library allocate -- code that
+ * runs under a fixed device-memory budget owned by another allocator, and
+ * latency-sensitive loops where an allocation, or the device-wide
+ * synchronisation a cudaFree implies, is not acceptable.
+ * Same arguments, arithmetic and outputs as tnmc_sample (precision TNMC_F64 or
+ * TNMC_F32).  The per-sample right-vector stacks live in one fixed 64 MiB
+ * static device array that every GPU loading the library holds until the
+ * process exits; when the stacks of all CTAs do not fit, fewer CTAs run (slower,
+ * same results).  A lattice whose single-CTA stack exceeds 64 MiB
+ * ((Lx+1) * P * 64 * 8 bytes in FP64, (Lx+1) * P * 128 * 4 in FP32) is rejected
+ * with TNMC_E_INVALID_ARG.  All calls on a device share the array: calls that
+ * overlap on the GPU race, so order them on one stream.  The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make it before any stream capture.
+ */
+tnmc_status tnmc_sample_noalloc(const tnmc_env* env, int precision, int64_t B, uint64_t seed,
+                                uint64_t sample_offset, int8_t* spins, double* logq, double* energy,
+                                int32_t* flags, void* stream);
+
+/*
  * Forced ("teacher") evaluation of log q and H for given configurations
  * (App. A, product of conditional ratios); same arithmetic as tnmc_sample.
  * spins       device int8 [B][Ly][Lx], values -1/+1 (input)

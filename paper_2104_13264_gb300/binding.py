@@ -49,6 +49,7 @@ SIGNATURES = {
     "tnmc_env_status": ([_P, ctypes.POINTER(ctypes.c_int32)], _INT),
     "tnmc_sample": ([_P, _INT, _I64, _U64, _U64, _P, _P, _P, _P, _P], _INT),
     "tnmc_logq": ([_P, _INT, _I64, _P, _P, _P, _P, _P], _INT),
+    "tnmc_sample_noalloc": ([_P, _INT, _I64, _U64, _U64, _P, _P, _P, _P, _P], _INT),
     "tnmc_init_chains": ([_P, _INT, _I64, _U64, _P, _P, _P, _P], _INT),
     "tnmc_mh_step": ([_P, _I64, _I64, _P, _P, _P, _P, _P, _P, _U64, _U64, _P, _P, _P], _INT),
 }
