@@ -158,6 +158,22 @@ def build_env(Jh, Jv, h, beta, chi):
     return env
 
 
+def round_bf16(x):
+    """Round FP64 values to the nearest bfloat16 (8 significant bits, ties to even)."""
+    x = np.asarray(x, dtype=np.float64)
+    m, e = np.frexp(x)                       # x = m 2^e, |m| in [0.5, 1)
+    e = np.maximum(e, -125)                  # bfloat16 shares float32's exponent range
+    return np.ldexp(np.round(np.ldexp(m, 8 + (np.frexp(x)[1] - e))), e - 8)
+
+
+def env_bf16(env):
+    """Copy of env whose tensors are rounded to bfloat16 (the BF16 contraction's operands)."""
+    out = Env(env.Lx, env.Ly, env.beta, env.chi, env.Jh, env.Jv, env.h)
+    out.M = [[round_bf16(t) for t in row] for row in env.M]
+    out.log_scale, out.log_lambda, out.logZ = env.log_scale, env.log_lambda, env.logZ
+    return out
+
+
 def _pow2_normalize(x):
     """Scale each row of x by the power of two that puts its max |x| in [1, 2)."""
     m = np.max(np.abs(x), axis=1)

@@ -85,8 +85,9 @@ tnmc_status tnmc_build_env(const tnmc_lattice* lat, double beta, int chi, int pr
   const size_t oM64 = take(tens * 8), oR64 = take(tens * 8);
   const size_t oL32 = (mask & (1 << TNMC_F32)) ? take(tens * 4) : 0;
   const size_t oR32 = (mask & (1 << TNMC_F32)) ? take(tens * 4) : 0;
-  const size_t oL16 = (mask & (1 << TNMC_BF16)) ? take(tens * 2) : 0;
-  const size_t oR16 = (mask & (1 << TNMC_BF16)) ? take(tens * 2) : 0;
+  const size_t oL16 = (mask & (1 << TNMC_BF16)) ? take(ntens * tnmc_tc_tile_bytes()) : 0;
+  const size_t oR16 = (mask & (1 << TNMC_BF16)) ? take(ntens * tnmc_tc_tile_bytes()) : 0;
+  const size_t oh32 = take(nh * 4), oJh32 = take((nJh ? nJh : 1) * 4), oJv32 = take((nJv ? nJv : 1) * 4);
   const size_t ols = take((size_t)Ly * 8), osv = take((size_t)Ly * (Lx + 1) * P * 8);
   const size_t odisc = take((size_t)Ly * (Lx + 1) * 8), ologZ = take(8), ostat = take(8);
   const size_t total = off;
@@ -133,6 +134,9 @@ tnmc_status tnmc_build_env(const tnmc_lattice* lat, double beta, int chi, int pr
   env->sv = reinterpret_cast<double*>(base + osv);
   env->discarded = reinterpret_cast<double*>(base + odisc);
   env->logZ = reinterpret_cast<double*>(base + ologZ);
+  env->h32 = reinterpret_cast<float*>(base + oh32);
+  env->Jh32 = reinterpret_cast<float*>(base + oJh32);
+  env->Jv32 = reinterpret_cast<float*>(base + oJv32);
 
   tnmc_status st = TNMC_OK;
   void* work = nullptr;
@@ -153,6 +157,8 @@ tnmc_status tnmc_build_env(const tnmc_lattice* lat, double beta, int chi, int pr
     st = tnmc_launch_build(env, s, work, wbytes);
     if (st != TNMC_OK) break;
     st = tnmc_launch_derive(env, mask, s);
+    if (st != TNMC_OK) break;
+    if (mask & (1 << TNMC_BF16)) st = tnmc_launch_derive_tc(env, s);
   } while (0);
   if (work) (void)cudaFreeAsync(work, s);
   if (st != TNMC_OK) {

@@ -17,6 +17,9 @@ constexpr int kMaxPad = 64;       // padded bond stride P <= 64
 //   M64   FP64 master, [Ly][Lx][P][2][P]  M[a][s][b]      (left layout)
 //   L{T}  sampler copy in precision T, same layout as M64
 //   R{T}  sampler copy in precision T, [Ly][Lx][P][P][2]  MT[b][a][s]
+//   L16 / R16 (BF16) instead hold the tensor-core operand tiles: per (r, c) a
+//         128 x 64 K-major 128-byte-swizzled tile (left: n = s*64 + b, k = a;
+//         right: n = s*64 + a, k = b), zero-padded to 64.
 //   fe    FP64 [Ly][Lx][2]: exp(-beta Jv[r-1][c]), exp(+beta Jv[r-1][c]); 1 for r = 0
 //   fe32  same in FP32
 // ---------------------------------------------------------------------------
@@ -57,6 +60,9 @@ struct tnmc_env {
   double* sv = nullptr;          // [Ly][Lx+1][P]
   double* discarded = nullptr;   // [Ly][Lx+1]
   double* logZ = nullptr;        // scalar
+  float* h32 = nullptr;          // FP32 couplings for the tensor-core sampler's energy
+  float* Jh32 = nullptr;
+  float* Jv32 = nullptr;
   tnmc::Scratch scratch;         // sampler scratch (grown on demand)
 };
 
@@ -152,6 +158,11 @@ tnmc_status tnmc_launch_derive(tnmc_env* env, int precision_mask, cudaStream_t s
 tnmc_status tnmc_launch_sample(const tnmc_env* env, int precision, int64_t B, uint64_t seed,
                                uint64_t sample_offset, const int8_t* spins_in, int8_t* spins_out,
                                double* logq, double* energy, int32_t* flags, cudaStream_t stream);
+tnmc_status tnmc_launch_derive_tc(tnmc_env* env, cudaStream_t stream);
+size_t tnmc_tc_tile_bytes();
+tnmc_status tnmc_launch_sample_tc(const tnmc_env* env, int64_t B, uint64_t seed, uint64_t offset,
+                                  const int8_t* spins_in, int8_t* spins_out, double* logq, double* energy,
+                                  int32_t* flags, cudaStream_t stream);
 tnmc_status tnmc_launch_mh(const tnmc_env* env, int64_t C, int64_t T, const int8_t* prop_spins,
                            const double* prop_logq, const double* prop_energy, int8_t* chain_spins,
                            double* chain_logq, double* chain_energy, uint64_t seed,

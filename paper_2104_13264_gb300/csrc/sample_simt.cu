@@ -130,11 +130,6 @@ tnmc_status tnmc_launch_derive(tnmc_env* env, int mask, cudaStream_t stream) {
     derive_kernel<float><<<1024, 256, 0, stream>>>(d, const_cast<float*>(d.L32), const_cast<float*>(d.R32), ntens);
     TNMC_CUDA_TRY(cudaGetLastError());
   }
-  if (mask & (1 << TNMC_BF16)) {
-    derive_kernel<__nv_bfloat16><<<1024, 256, 0, stream>>>(d, const_cast<__nv_bfloat16*>(d.L16),
-                                                          const_cast<__nv_bfloat16*>(d.R16), ntens);
-    TNMC_CUDA_TRY(cudaGetLastError());
-  }
   return TNMC_OK;
 }
 
@@ -150,6 +145,8 @@ tnmc_status tnmc_launch_sample(const tnmc_env* env, int precision, int64_t B, ui
   if (precision == TNMC_F32)
     return launch_sample_t<float, 128>(env, d.L32, d.R32, d.fe32, B, seed, offset, spins_in, spins_out, logq,
                                        energy, flags, stream);
-  tnmc_set_error("precision %d has no sampler yet", precision);
+  if (precision == TNMC_BF16)
+    return tnmc_launch_sample_tc(env, B, seed, offset, spins_in, spins_out, logq, energy, flags, stream);
+  tnmc_set_error("unknown precision %d", precision);
   return TNMC_E_UNSUPPORTED;
 }
