@@ -3,6 +3,7 @@
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <new>
@@ -81,7 +82,7 @@ tnmc_status tnmc_build_env(const tnmc_lattice* lat, double beta, int chi, int pr
   };
   const size_t oJh = take((nJh ? nJh : 1) * 8), oJv = take((nJv ? nJv : 1) * 8), oh = take(nh * 8);
   const size_t ofe = take(nh * 2 * 8), ofe32 = take(nh * 2 * 4);
-  const size_t obond = take((size_t)Ly * (Lx + 1) * 4);
+  const size_t obond = take((size_t)Ly * (Lx + 1) * 4), oesz = take((size_t)Ly * (Lx + 1) * 4);
   const size_t oM64 = take(tens * 8), oR64 = take(tens * 8);
   const size_t oL32 = (mask & (1 << TNMC_F32)) ? take(tens * 4) : 0;
   const size_t oR32 = (mask & (1 << TNMC_F32)) ? take(tens * 4) : 0;
@@ -117,6 +118,12 @@ tnmc_status tnmc_build_env(const tnmc_lattice* lat, double beta, int chi, int pr
   d.beta = beta;
   d.integer_couplings = is_integer_array(lat->h, nh) && (nJh == 0 || is_integer_array(lat->Jh, nJh)) &&
                         (nJv == 0 || is_integer_array(lat->Jv, nJv));
+  {
+    bool zero_field = true;
+    for (size_t i = 0; i < nh; ++i) zero_field = zero_field && (lat->h[i] == 0.0);
+    const char* force = getenv("TNMC_DENSE_BUILDER");   // testing knob: the dense path on h = 0 lattices
+    d.z2 = zero_field && !(force && force[0] == '1');
+  }
   d.Jh = reinterpret_cast<const double*>(base + oJh);
   d.Jv = reinterpret_cast<const double*>(base + oJv);
   d.h = reinterpret_cast<const double*>(base + oh);
@@ -134,6 +141,7 @@ tnmc_status tnmc_build_env(const tnmc_lattice* lat, double beta, int chi, int pr
   env->sv = reinterpret_cast<double*>(base + osv);
   env->discarded = reinterpret_cast<double*>(base + odisc);
   env->logZ = reinterpret_cast<double*>(base + ologZ);
+  env->esz = reinterpret_cast<int32_t*>(base + oesz);
   env->h32 = reinterpret_cast<float*>(base + oh32);
   env->Jh32 = reinterpret_cast<float*>(base + oJh32);
   env->Jv32 = reinterpret_cast<float*>(base + oJv32);

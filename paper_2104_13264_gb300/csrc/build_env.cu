@@ -41,6 +41,7 @@ struct BuildArgs {
   double* logZ;
   double* work;   // (Lx + 2) slots of 8 P^2 doubles
   int32_t* status;
+  int32_t* esz;   // [Ly][Lx+1] even-sector size of every bond (Z2 builder)
 };
 
 
@@ -312,16 +313,24 @@ __device__ inline void tournament(int t, int i, int N, int& p, int& q) {
 }
 
 // One-sided Jacobi (Hestenes): orthogonalise the m <= 128 rows (length n, stride
-// ld) of J.  Round-robin pairing; four lanes own one pair (all m/2 pairs of a
-// round run at once on 256 threads).  Squared row norms d[] are maintained
-// through the exact update alpha' = alpha - t gamma, beta' = beta + t gamma and
-// recomputed at the start of every sweep.  A pair is rotated while
-// |gamma| > tol sqrt(alpha beta); tol = 1e-13 sits above the rounding level of a
-// length-128 dot product, so the sweep count stays small.
+// ld) of J.  Round-robin pairing; a group of L lanes owns one pair, with L chosen
+// so that all m/2 pairs of a round run at once on the 256 threads.  Squared row
+// norms d[] are maintained through the exact update alpha' = alpha - t gamma,
+// beta' = beta + t gamma and recomputed at the start of every sweep.  A pair is
+// rotated while |gamma| > tol sqrt(alpha beta), tol = 1e-13 (above the rounding
+// level of a dot product of length <= 128).  Rows whose norm is below 1e-13 of
+// the largest are at the rounding level of the matrix: they carry no information
+// and are left out of the rotations (callers treat them as zero rows).
+constexpr double kJacobiTol = 1e-13;
+constexpr double kNullRel = 1e-13;
+
 __device__ void jacobi_rows(double* J, int m, int n, int ld, double* d, int* flag) {
-  const int quad = threadIdx.x >> 2, ql = threadIdx.x & 3;
   const int N = m + (m & 1);
-  const double tol = 1e-13;
+  const int npairs = N / 2;
+  // four lanes per pair: the FP64 pipe, not the thread count, bounds this loop,
+  // and the per-pair scalar work is repeated on every lane of a group
+  const int L = 4;
+  const int grp = threadIdx.x / L, gl = threadIdx.x % L;
   for (int sweep = 0; sweep < 40; ++sweep) {
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
       double s = 0.0;
@@ -330,37 +339,51 @@ __device__ void jacobi_rows(double* J, int m, int n, int ld, double* d, int* fla
     }
     if (threadIdx.x == 0) flag[0] = 0;
     __syncthreads();
+    double dmax = 0.0;
+    for (int i = 0; i < m; ++i) dmax = fmax(dmax, d[i]);
+    const double dnull = kNullRel * kNullRel * dmax;
     for (int t = 0; t < N - 1; ++t) {
-      int p = -1, q = -1;
-      if (quad < N / 2) tournament(t, quad, N, p, q);
-      const bool live = (quad < N / 2) && p < m && q < m;
-      double ga = 0.0;
-      double* rp = J + (size_t)(live ? p : 0) * ld;
-      double* rq = J + (size_t)(live ? q : 0) * ld;
-      if (live)
-        for (int x = ql; x < n; x += 4) ga += rp[x] * rq[x];
-      ga += __shfl_xor_sync(0xffffffffu, ga, 1);
-      ga += __shfl_xor_sync(0xffffffffu, ga, 2);
-      if (live) {
-        const double al = d[p], be = d[q];
-        if (ga != 0.0 && fabs(ga) > tol * sqrt(al * be)) {
-          const double zeta = (be - al) / (2.0 * ga);
-          double tt;
-          if (fabs(zeta) > 1e150)
-            tt = 0.5 / zeta;
-          else
-            tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          const double cs = 1.0 / sqrt(1.0 + tt * tt);
-          const double sn = cs * tt;
-          for (int x = ql; x < n; x += 4) {
-            const double u = rp[x], v = rq[x];
-            rp[x] = cs * u - sn * v;
-            rq[x] = sn * u + cs * v;
-          }
-          if (ql == 0) {
-            d[p] = al - tt * ga;
-            d[q] = be + tt * ga;
-            flag[0] = 1;
+      {
+        // every lane runs the group shuffles below (full-warp masks); groups beyond
+        // the round's pairs only contribute zeros.  m <= 128 gives at most 64 pairs,
+        // one per group of four lanes on 256 threads.
+        int p = m, q = m;
+        if (grp < npairs) tournament(t, grp, N, p, q);
+        const bool live = p < m && q < m;
+        double ga = 0.0;
+        double* rp = J + (size_t)(live ? p : 0) * ld;
+        double* rq = J + (size_t)(live ? q : 0) * ld;
+        if (live)
+          for (int x = gl; x < n; x += L) ga += rp[x] * rq[x];
+        for (int o = 1; o < L; o <<= 1) ga += __shfl_xor_sync(0xffffffffu, ga, o);
+        if (live) {
+          const double al = d[p], be = d[q];
+          if (ga != 0.0 && al > dnull && be > dnull && ga * ga > kJacobiTol * kJacobiTol * al * be) {
+            // tangent of the rotation angle in FP32 (its accuracy only sets the
+            // convergence rate); cos from it by two FP64 Newton steps for 1/sqrt, so the
+            // applied rotation is orthogonal to FP64 rounding whatever t is
+            float zeta = (float)(be - al) / (2.0f * (float)ga);
+            if (!isfinite(zeta)) zeta = (float)((be - al) / (2.0 * ga));   // outside FP32 range
+            float tf;
+            if (fabsf(zeta) > 1e18f) tf = 0.5f / zeta;
+            else tf = (zeta >= 0.0f ? 1.0f : -1.0f) / (fabsf(zeta) + sqrtf(1.0f + zeta * zeta));
+            const double tt = (double)tf;
+            const double x = fma(tt, tt, 1.0);
+            double cs = (double)rsqrtf((float)x);
+            cs = cs * fma(-0.5 * x, cs * cs, 1.5);
+            cs = cs * fma(-0.5 * x, cs * cs, 1.5);
+            const double sn = cs * tt;
+            for (int xx = gl; xx < n; xx += L) {
+              const double u = rp[xx], v = rq[xx];
+              rp[xx] = cs * u - sn * v;
+              rq[xx] = sn * u + cs * v;
+            }
+            if (gl == 0) {
+              const double c2 = cs * cs;
+              d[p] = c2 * fma(tt * tt, be, fma(-2.0 * tt, ga, al));
+              d[q] = c2 * fma(tt * tt, al, fma(2.0 * tt, ga, be));
+              flag[0] = 1;
+            }
           }
         }
       }
@@ -439,39 +462,11 @@ __device__ double svd_sweep(const BuildArgs& a, Shared& sh, int r) {
       const int j = idx / n, x = idx % n;
       const int i = sh.sel[j];
       const double nv = nrm[i];
-      Vt[idx] = (nv > 1e-280) ? J[i * ld + x] / nv : 0.0;
+      Vt[idx] = (nv > kNullRel * smax) ? J[i * ld + x] / nv : 0.0;
     }
     __syncthreads();
-    // orthonormal completion for (numerically) zero rows -- rare, one warp
-    if (w == 0) {
-      for (int j = 0; j < kk; ++j) {
-        if (nrm[sh.sel[j]] > 1e-280) continue;
-        for (int e = 0; e < n; ++e) {
-          for (int x = lane; x < n; x += 32) Vt[j * n + x] = (x == e) ? 1.0 : 0.0;
-          __syncwarp();
-          for (int pass = 0; pass < 2; ++pass) {
-            for (int i = 0; i < kk; ++i) {
-              if (i == j) continue;
-              if (nrm[sh.sel[i]] <= 1e-280 && i > j) continue;
-              double d = 0.0;
-              for (int x = lane; x < n; x += 32) d += Vt[i * n + x] * Vt[j * n + x];
-              d = warp_sum(d);
-              for (int x = lane; x < n; x += 32) Vt[j * n + x] -= d * Vt[i * n + x];
-              __syncwarp();
-            }
-          }
-          double s = 0.0;
-          for (int x = lane; x < n; x += 32) s += Vt[j * n + x] * Vt[j * n + x];
-          s = sqrt(warp_sum(s));
-          if (s > 0.5) {
-            for (int x = lane; x < n; x += 32) Vt[j * n + x] /= s;
-            __syncwarp();
-            break;
-          }
-        }
-      }
-    }
-    __syncthreads();
+    // kept rows at the rounding level (norm <= 1e-13 of the largest) stay zero rows:
+    // they carry no weight, so the MPS and q are unchanged
     // US = A V_k / smax  (m x kk), A from the original slot
     const double inv = 1.0 / smax;
     for (int idx = threadIdx.x; idx < m * kk; idx += blockDim.x) {
@@ -592,6 +587,414 @@ __global__ void __launch_bounds__(kBuildThreads) build_env_kernel(BuildArgs a) {
   }
 }
 
+// ===========================================================================
+// Z2-symmetric builder (all fields h = 0).
+//
+// With h = 0 the Boltzmann weight is invariant under a global spin flip, so every
+// environment is an even function of its row.  In the parity basis
+// |0> = (|-1> + |+1>)/sqrt2, |1> = (|-1> - |+1>)/sqrt2 of each site the vertical
+// transfer exp(beta J s s') is diagonal (2 cosh, 2 sinh), a horizontal bond is
+// cosh I(x)I + sinh X(x)X (X flips the parity), and every bond index carries a
+// parity.  Each site matrix of the QR sweep and of the SVD sweep is then block
+// diagonal with one block per parity sector; the sectors are factored separately
+// (the SVD blocks are half the size of the dense ones, a quarter of the Jacobi
+// work) and the chi largest singular values are kept across both sectors.  The
+// truncated MPS is the dense algorithm's up to gauge.  Bonds store their even
+// sector first: index i of a bond with e even states has parity (i >= e).
+// The finished row is written back in the spin basis.
+// ===========================================================================
+
+struct ShZ2 {
+  double* W;
+  int* slot;     // [Lx + 2]
+  int* bdim;     // [Lx + 1] dimension of bond c
+  int* bev;      // [Lx + 1] even-sector size of bond c
+  int* sel;      // [2P] kept rows by global rank
+  int* sec;      // [2P] scratch: (sector, rank within sector) per kept row
+  double* red;
+  int* flag;
+};
+
+// position of (a, k) in a doubled bond built from a bond of size D with e even states
+__device__ inline int dbl_idx(int a, int k, int D, int e) {
+  const bool odd = a >= e;
+  if (k == 0) return odd ? D + (a - e) : a;
+  return odd ? a : D + (D - e) + a;
+}
+__device__ inline void dbl_inv(int l, int D, int e, int& a, int& k) {
+  if (l < D) {
+    a = l;
+    k = (l < e) ? 0 : 1;
+  } else {
+    const int j = l - D;
+    if (j < D - e) { a = e + j; k = 0; }
+    else { a = j - (D - e); k = 1; }
+  }
+}
+
+__device__ void apply_row_mpo_z2(const BuildArgs& a, ShZ2& sh, int r) {
+  const int Lx = a.Lx, P = a.P;
+  const size_t slot_sz = (size_t)8 * P * P;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const double isq2 = 0.70710678118654752440;
+  for (int c = w; c < Lx; c += kWarps) {
+    const bool last_row = (r == a.Ly - 1);
+    const int Dl0 = last_row ? 1 : a.bond[(r + 1) * (Lx + 1) + c];
+    const int Dr0 = last_row ? 1 : a.bond[(r + 1) * (Lx + 1) + c + 1];
+    const int el0 = last_row ? 1 : a.esz[(r + 1) * (Lx + 1) + c];
+    const int er0 = last_row ? 1 : a.esz[(r + 1) * (Lx + 1) + c + 1];
+    const bool kl = c > 0, kr = c < Lx - 1;
+    const int Dl = kl ? 2 * Dl0 : Dl0, Dr = kr ? 2 * Dr0 : Dr0;
+    double lam0 = 1.0, lam1 = 1.0, w0 = 1.0, w1 = 0.0;
+    if (!last_row) {
+      const double jv = a.Jv[r * Lx + c];
+      lam0 = exp(a.beta * jv) + exp(-a.beta * jv);
+      lam1 = exp(a.beta * jv) - exp(-a.beta * jv);
+    }
+    if (kr) {
+      const double jh = a.Jh[r * (Lx - 1) + c];
+      w0 = 0.5 * (exp(a.beta * jh) + exp(-a.beta * jh));
+      w1 = 0.5 * (exp(a.beta * jh) - exp(-a.beta * jh));
+    }
+    const double* Mn = last_row ? nullptr : a.M64 + ((size_t)(r + 1) * Lx + c) * P * 2 * P;
+    double* out = a.work + (size_t)c * slot_sz;
+    const int total = Dl * 2 * Dr;
+    for (int idx = lane; idx < total; idx += 32) {
+      const int rr = idx % Dr, tau = (idx / Dr) & 1, l = idx / (2 * Dr);
+      int aa = l, kin = 0, b = rr, kout = 0;
+      if (kl) dbl_inv(l, Dl0, el0, aa, kin);
+      if (kr) dbl_inv(rr, Dr0, er0, b, kout);
+      const int tp = tau ^ kin ^ kout;   // X^(kin + kout) acting on the site
+      double n;
+      if (last_row) {
+        n = (tp == 0) ? 1.4142135623730950488 : 0.0;
+      } else {
+        const double m0 = Mn[((size_t)aa * 2 + 0) * P + b];
+        const double m1 = Mn[((size_t)aa * 2 + 1) * P + b];
+        n = (tp == 0) ? lam0 * (m0 + m1) * isq2 : lam1 * (m0 - m1) * isq2;
+      }
+      out[idx] = kr ? (kout ? w1 : w0) * n : n;
+    }
+    if (lane == 0) {
+      sh.slot[c] = c;
+      sh.bdim[c] = Dl;
+      sh.bev[c] = kl ? Dl0 : el0;
+      if (c == Lx - 1) {
+        sh.bdim[Lx] = Dr;
+        sh.bev[Lx] = er0;
+      }
+    }
+  }
+  if (threadIdx.x == 0) {
+    sh.slot[Lx] = Lx;
+    sh.slot[Lx + 1] = Lx + 1;
+  }
+  __syncthreads();
+}
+
+__device__ double qr_sweep_z2(const BuildArgs& a, ShZ2& sh) {
+  const int Lx = a.Lx, P = a.P;
+  const size_t slot_sz = (size_t)8 * P * P;
+  double logs = 0.0;
+  double* A = sh.W;
+  double* Q = sh.W + 2 * P * P;
+  double* Rb = sh.W + 4 * P * P;
+  double* tau = sh.W + 6 * P * P;
+  double* diag = tau + P;
+  for (int c = 0; c < Lx - 1; ++c) {
+    const int Dl = sh.bdim[c], el = sh.bev[c], Dr = sh.bdim[c + 1], er = sh.bev[c + 1];
+    const int n0 = er, n1 = Dr - er;
+    const int k0 = min(Dl, n0), k1 = min(Dl, n1), K = k0 + k1;
+    const double* X = a.work + (size_t)sh.slot[c] * slot_sz;
+    double* Tn = a.work + (size_t)sh.slot[Lx] * slot_sz;   // new site c: [Dl][2][K]
+    for (int idx = threadIdx.x; idx < Dl * 2 * K; idx += blockDim.x) Tn[idx] = 0.0;
+    __syncthreads();
+    for (int s = 0; s < 2; ++s) {
+      const int ns = s ? n1 : n0, col0 = s ? er : 0, ks = s ? k1 : k0, j0 = s ? k0 : 0;
+      if (ns == 0) continue;
+      for (int idx = threadIdx.x; idx < Dl * ns; idx += blockDim.x) {
+        const int j = idx / Dl, l = idx % Dl;
+        const int tl = s ^ (l >= el ? 1 : 0);
+        A[idx] = X[((size_t)l * 2 + tl) * Dr + col0 + j];
+      }
+      __syncthreads();
+      householder_qr(A, Dl, ns, Q, Rb + s * P * P, tau, diag);
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < Dl * ks; idx += blockDim.x) {
+        const int j = idx / Dl, l = idx % Dl;
+        const int tl = s ^ (l >= el ? 1 : 0);
+        Tn[((size_t)l * 2 + tl) * K + j0 + j] = Q[j * Dl + l];
+      }
+      __syncthreads();
+    }
+    double mx = 0.0;
+    for (int idx = threadIdx.x; idx < k0 * n0; idx += blockDim.x) mx = fmax(mx, fabs(Rb[idx]));
+    for (int idx = threadIdx.x; idx < k1 * n1; idx += blockDim.x) mx = fmax(mx, fabs(Rb[P * P + idx]));
+    mx = block_max(mx, sh.red);
+    if (!(mx > 0.0) || !isfinite(mx)) {
+      if (threadIdx.x == 0) set_status(a.status, TNMC_E_NUMERIC);
+      mx = 1.0;
+    }
+    logs += log(mx);
+    const double inv = 1.0 / mx;
+    const double* O = a.work + (size_t)sh.slot[c + 1] * slot_sz;
+    double* Nn = a.work + (size_t)sh.slot[Lx + 1] * slot_sz;
+    const int ncol = 2 * sh.bdim[c + 2 > Lx ? Lx : c + 2];   // (tau, x) of site c+1
+    for (int idx = threadIdx.x; idx < K * ncol; idx += blockDim.x) {
+      const int jp = idx / ncol, col = idx % ncol;
+      const int s = jp >= k0 ? 1 : 0;
+      const int j = s ? jp - k0 : jp;
+      const int ns = s ? n1 : n0, col0 = s ? er : 0;
+      const double* Rk = Rb + s * P * P + j * ns;
+      double acc = 0.0;
+      for (int i = j; i < ns; ++i) acc += Rk[i] * O[(size_t)(col0 + i) * ncol + col];
+      Nn[idx] = acc * inv;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int t = sh.slot[c];
+      sh.slot[c] = sh.slot[Lx];
+      sh.slot[Lx] = t;
+      t = sh.slot[c + 1];
+      sh.slot[c + 1] = sh.slot[Lx + 1];
+      sh.slot[Lx + 1] = t;
+      sh.bdim[c + 1] = K;
+      sh.bev[c + 1] = k0;
+    }
+    __syncthreads();
+  }
+  return logs;
+}
+
+// column j of parity block s of a site matrix with right bond (Dr, er): (tau, x)
+__device__ inline int z2_col(int s, int j, int Dr, int er) {
+  const int ns0 = s ? Dr - er : er;              // tau = 0 part: x in sector s
+  if (j < ns0) return (s ? er : 0) + j;           // tau = 0
+  return Dr + (s ? 0 : er) + (j - ns0);           // tau = 1, x in sector 1 - s
+}
+
+__device__ double svd_sweep_z2(const BuildArgs& a, ShZ2& sh, int r) {
+  const int Lx = a.Lx, P = a.P;
+  const size_t slot_sz = (size_t)8 * P * P;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  double logs = 0.0;
+  for (int c = Lx - 1; c >= 1; --c) {
+    const int Dl = sh.bdim[c], el = sh.bev[c], Dr = sh.bdim[c + 1], er = sh.bev[c + 1];
+    const int n = Dr;                 // columns of each parity block
+    const int ld = n + 1;
+    double* J = sh.W;                 // [Dl][ld]: sector-0 rows, then sector-1 rows
+    double* US = sh.W + 4 * P * P + 2 * P;
+    double* nrm = sh.W + 6 * P * P + 2 * P;
+    const double* A = a.work + (size_t)sh.slot[c] * slot_sz;   // [Dl][2][Dr]
+    const int kk = bond_dim_dev(a.chi, Lx, a.Ly, r, c);
+    if (kk > Dl) {
+      if (threadIdx.x == 0) set_status(a.status, TNMC_E_NUMERIC);
+      return logs;
+    }
+    for (int idx = threadIdx.x; idx < Dl * n; idx += blockDim.x) {
+      const int l = idx / n, j = idx % n;
+      const int s = l >= el ? 1 : 0;
+      const int col = z2_col(s, j, Dr, er);     // tau * Dr + x
+      J[l * ld + j] = A[(size_t)l * 2 * Dr + col];
+    }
+    __syncthreads();
+    if (el > 0) jacobi_rows(J, el, n, ld, nrm, sh.flag);
+    if (Dl - el > 0) jacobi_rows(J + (size_t)el * ld, Dl - el, n, ld, nrm + el, sh.flag);
+    for (int i = w; i < Dl; i += kWarps) {
+      double sq = 0.0;
+      for (int x = lane; x < n; x += 32) sq += J[i * ld + x] * J[i * ld + x];
+      sq = warp_sum(sq);
+      if (lane == 0) nrm[i] = sqrt(sq);
+    }
+    __syncthreads();
+    // global rank (descending norm, ties by index); kept rows listed sector by sector
+    for (int i = threadIdx.x; i < Dl; i += blockDim.x) {
+      int rank = 0, rs = 0;
+      const double ni = nrm[i];
+      const int si = i >= el;
+      for (int j = 0; j < Dl; ++j) {
+        const double nj = nrm[j];
+        const int before = (nj > ni) || (nj == ni && j < i);
+        rank += before;
+        if (before && ((j >= el) == si)) ++rs;   // kept-candidates of the same sector ranked above
+      }
+      sh.sec[i] = (rank < kk) ? (si << 16 | rs) : -1;
+      if (rank < kk) sh.sel[rank] = i;
+    }
+    __syncthreads();
+    // sector counts of the kept rows
+    if (threadIdx.x == 0) {
+      int k0 = 0;
+      for (int q = 0; q < kk; ++q) k0 += (sh.sel[q] < el);
+      sh.flag[1] = k0;
+    }
+    __syncthreads();
+    const int k0 = sh.flag[1];
+    double tot = 0.0, dsc = 0.0;
+    for (int i = threadIdx.x; i < Dl; i += blockDim.x) {
+      tot += nrm[i] * nrm[i];
+      if (sh.sec[i] < 0) dsc += nrm[i] * nrm[i];
+    }
+    tot = block_sum(tot, sh.red);
+    dsc = block_sum(dsc, sh.red);
+    const double smax = nrm[sh.sel[0]];
+    if (!(smax > 0.0) || !isfinite(smax)) {
+      if (threadIdx.x == 0) set_status(a.status, TNMC_E_NUMERIC);
+      return logs;
+    }
+    double* svr = a.sv + ((size_t)r * (Lx + 1) + c) * P;
+    for (int j = threadIdx.x; j < P; j += blockDim.x) svr[j] = (j < kk) ? nrm[sh.sel[j]] / sqrt(tot) : 0.0;
+    if (threadIdx.x == 0) a.disc[r * (Lx + 1) + c] = dsc / tot;
+    // new site c: [kk][2][Dr]; kept row i of sector s with in-sector rank j sits at s ? k0 + j : j
+    double* Vt = a.work + (size_t)sh.slot[Lx] * slot_sz;
+    for (int idx = threadIdx.x; idx < kk * 2 * Dr; idx += blockDim.x) Vt[idx] = 0.0;
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < Dl * n; idx += blockDim.x) {
+      const int i = idx / n, j = idx % n;
+      const int code = sh.sec[i];
+      if (code < 0) continue;
+      const int s = code >> 16, rs = code & 0xFFFF;
+      const int row = s ? k0 + rs : rs;
+      const double nv = nrm[i];
+      Vt[(size_t)row * 2 * Dr + z2_col(s, j, Dr, er)] = (nv > kNullRel * smax) ? J[i * ld + j] / nv : 0.0;
+    }
+    __syncthreads();
+    // kept rows at the rounding level stay zero rows (no weight; q unchanged)
+    // US (Dl x kk, block diagonal) = A V / smax
+    const double inv = 1.0 / smax;
+    for (int idx = threadIdx.x; idx < Dl * kk; idx += blockDim.x) {
+      const int i = idx / kk, jp = idx % kk;
+      const int si = i >= el, sj = jp >= k0;
+      double acc = 0.0;
+      if (si == sj) {
+        const double* Ar = A + (size_t)i * 2 * Dr;
+        const double* Vr = Vt + (size_t)jp * 2 * Dr;
+        for (int j = 0; j < n; ++j) {
+          const int col = z2_col(si, j, Dr, er);
+          acc += Ar[col] * Vr[col];
+        }
+      }
+      US[idx] = acc * inv;
+    }
+    __syncthreads();
+    logs += log(smax);
+    // absorb into site c-1: rows (y, tau) of length Dl -> kk, block by block
+    const double* O = a.work + (size_t)sh.slot[c - 1] * slot_sz;
+    double* Nn = a.work + (size_t)sh.slot[Lx + 1] * slot_sz;
+    const int rows = sh.bdim[c - 1] * 2;
+    for (int idx = threadIdx.x; idx < rows * kk; idx += blockDim.x) {
+      const int q = idx / kk, jp = idx % kk;
+      const int sj = jp >= k0;
+      const int i0 = sj ? el : 0, i1 = sj ? Dl : el;
+      double acc = 0.0;
+      for (int i = i0; i < i1; ++i) acc += O[(size_t)q * Dl + i] * US[i * kk + jp];
+      Nn[idx] = acc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int t = sh.slot[c];
+      sh.slot[c] = sh.slot[Lx];
+      sh.slot[Lx] = t;
+      t = sh.slot[c - 1];
+      sh.slot[c - 1] = sh.slot[Lx + 1];
+      sh.slot[Lx + 1] = t;
+      sh.bdim[c] = kk;
+      sh.bev[c] = k0;
+    }
+    __syncthreads();
+  }
+  return logs;
+}
+
+__global__ void __launch_bounds__(kBuildThreads) build_env_z2_kernel(BuildArgs a) {
+  extern __shared__ double smem[];
+  const int Lx = a.Lx, P = a.P;
+  ShZ2 sh;
+  sh.W = smem;
+  sh.red = smem + 6 * P * P + 4 * P;
+  int* ip = reinterpret_cast<int*>(sh.red + 64);
+  sh.slot = ip;
+  sh.bdim = ip + (Lx + 2);
+  sh.bev = sh.bdim + (Lx + 1);
+  sh.sel = sh.bev + (Lx + 1);
+  sh.sec = sh.sel + 2 * P;
+  sh.flag = sh.sec + 2 * P;
+  const size_t slot_sz = (size_t)8 * P * P;
+  const double isq2 = 0.70710678118654752440;
+
+  for (int r = a.Ly - 1; r >= 0; --r) {
+    apply_row_mpo_z2(a, sh, r);
+    double logs = qr_sweep_z2(a, sh);
+    logs += svd_sweep_z2(a, sh, r);
+    const double* T0 = a.work + (size_t)sh.slot[0] * slot_sz;
+    const int cnt = sh.bdim[0] * 2 * sh.bdim[1];
+    double sq = 0.0;
+    for (int idx = threadIdx.x; idx < cnt; idx += blockDim.x) sq += T0[idx] * T0[idx];
+    sq = block_sum(sq, sh.red);
+    const double n0 = sqrt(sq);
+    if (!(n0 > 0.0) || !isfinite(n0)) {
+      if (threadIdx.x == 0) set_status(a.status, TNMC_E_NUMERIC);
+    }
+    logs += log(n0);
+    // write the row in the spin basis: M[.][-1][.] = (T0 + T1)/sqrt2, M[.][+1][.] = (T0 - T1)/sqrt2
+    for (int c = 0; c < Lx; ++c) {
+      const int Dl = sh.bdim[c], Dr = sh.bdim[c + 1];
+      const double* T = a.work + (size_t)sh.slot[c] * slot_sz;
+      double* out = a.M64 + ((size_t)r * Lx + c) * P * 2 * P;
+      const double scale = ((c == 0) ? 1.0 / n0 : 1.0) * isq2;
+      for (int idx = threadIdx.x; idx < P * 2 * P; idx += blockDim.x) {
+        const int b = idx % P, s2 = (idx / P) & 1, aa = idx / (2 * P);
+        double v = 0.0;
+        if (aa < Dl && b < Dr) {
+          const double t0 = T[((size_t)aa * 2 + 0) * Dr + b], t1 = T[((size_t)aa * 2 + 1) * Dr + b];
+          v = (s2 == 0 ? t0 + t1 : t0 - t1) * scale;
+        }
+        out[idx] = v;
+      }
+      if (threadIdx.x == 0) {
+        a.bond[r * (Lx + 1) + c] = Dl;
+        a.esz[r * (Lx + 1) + c] = sh.bev[c];
+        if (Dl != bond_dim_dev(a.chi, Lx, a.Ly, r, c)) set_status(a.status, TNMC_E_NUMERIC);
+      }
+    }
+    if (threadIdx.x == 0) {
+      a.bond[r * (Lx + 1) + Lx] = 1;
+      a.esz[r * (Lx + 1) + Lx] = 1;
+      a.log_scale[r] = logs;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    double* v = sh.W;
+    double* v2 = sh.W + P;
+    for (int i = lane; i < P; i += 32) v[i] = (i == 0) ? 1.0 : 0.0;
+    __syncwarp();
+    double logv = 0.0;
+    for (int c = 0; c < Lx; ++c) {
+      const double* M = a.M64 + (size_t)c * P * 2 * P;
+      const int Dl = a.bond[c], Dr = a.bond[c + 1];
+      double mx = 0.0;
+      for (int b = lane; b < Dr; b += 32) {
+        double acc = 0.0;
+        for (int aa = 0; aa < Dl; ++aa) acc += v[aa] * (M[((size_t)aa * 2) * P + b] + M[((size_t)aa * 2 + 1) * P + b]);
+        v2[b] = acc;
+        mx = fmax(mx, fabs(acc));
+      }
+      mx = warp_max(mx);
+      __syncwarp();
+      for (int b = lane; b < P; b += 32) v[b] = (b < Dr && mx > 0.0) ? v2[b] / mx : 0.0;
+      if (mx > 0.0) logv += log(mx);
+      __syncwarp();
+    }
+    if (lane == 0) {
+      double tot = 0.0;
+      for (int r = 0; r < a.Ly; ++r) tot += a.log_scale[r];
+      *a.logZ = (v[0] > 0.0) ? tot + logv + log(v[0]) : NAN;
+    }
+  }
+}
+
 }  // namespace
 }  // namespace tnmc
 
@@ -601,7 +1004,7 @@ size_t tnmc_build_work_bytes(int Lx, int Ly, int P) {
 }
 
 static size_t build_smem_bytes(int Lx, int P) {
-  return (size_t)(6 * P * P + 4 * P + 64) * sizeof(double) + (size_t)(3 * Lx + 4 + 2 * P + 8) * sizeof(int);
+  return (size_t)(6 * P * P + 4 * P + 64) * sizeof(double) + (size_t)(3 * Lx + 4 + 4 * P + 8) * sizeof(int);
 }
 
 tnmc_status tnmc_launch_build(tnmc_env* env, cudaStream_t stream, void* work, size_t work_bytes) {
@@ -628,6 +1031,7 @@ tnmc_status tnmc_launch_build(tnmc_env* env, cudaStream_t stream, void* work, si
   a.logZ = env->logZ;
   a.work = static_cast<double*>(work);
   a.status = d.status;
+  a.esz = env->esz;
   const size_t smem = build_smem_bytes(d.Lx, d.P);
   int dev = 0, max_optin = 0;
   TNMC_CUDA_TRY(cudaGetDevice(&dev));
@@ -636,8 +1040,13 @@ tnmc_status tnmc_launch_build(tnmc_env* env, cudaStream_t stream, void* work, si
     tnmc_set_error("builder needs %zu bytes of shared memory (device allows %d): Lx too large", smem, max_optin);
     return TNMC_E_UNSUPPORTED;
   }
-  TNMC_CUDA_TRY(cudaFuncSetAttribute(build_env_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  build_env_kernel<<<1, kBuildThreads, smem, stream>>>(a);
+  if (d.z2) {
+    TNMC_CUDA_TRY(cudaFuncSetAttribute(build_env_z2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    build_env_z2_kernel<<<1, kBuildThreads, smem, stream>>>(a);
+  } else {
+    TNMC_CUDA_TRY(cudaFuncSetAttribute(build_env_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    build_env_kernel<<<1, kBuildThreads, smem, stream>>>(a);
+  }
   TNMC_CUDA_TRY(cudaGetLastError());
   return TNMC_OK;
 }

@@ -27,6 +27,7 @@ struct DeviceEnv {
   int Lx, Ly, chi, P;
   double beta;
   int integer_couplings;
+  int z2;             // 1 when every field is zero: the builder uses parity sectors
   const double* Jh;   // device copies of the couplings
   const double* Jv;
   const double* h;
@@ -60,6 +61,7 @@ struct tnmc_env {
   double* sv = nullptr;          // [Ly][Lx+1][P]
   double* discarded = nullptr;   // [Ly][Lx+1]
   double* logZ = nullptr;        // scalar
+  int32_t* esz = nullptr;        // [Ly][Lx+1] even-sector size per bond (Z2 builder)
   float* h32 = nullptr;          // FP32 couplings for the tensor-core sampler's energy
   float* Jh32 = nullptr;
   float* Jv32 = nullptr;

@@ -135,7 +135,7 @@ __device__ inline void unit_row(float* v) {
 
 __device__ inline void prefetch_l1(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
 
-__global__ void __launch_bounds__(kTile) sample_tc_kernel(TcArgs a) {
+__global__ void __launch_bounds__(kTile, 2) sample_tc_kernel(TcArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   unsigned char* sHi = base;
@@ -177,11 +177,16 @@ __global__ void __launch_bounds__(kTile) sample_tc_kernel(TcArgs a) {
   const uint32_t tmem = misc[0];
   const uint32_t tlane = tmem + ((uint32_t)(32 * warp) << 16);
 
-  auto tile_of = [&](int64_t g) -> const __nv_bfloat16* {
-    const int64_t rem = g % ((int64_t)Ly * S);
-    const int r = (int)(rem / S);
-    const StepPos p = decode_step((int)(rem % S), Lx);
-    return (p.left ? a.TL : a.TR) + ((size_t)r * Lx + p.c) * (kN * kK);
+  // producer position (row, step within the row) of the next tile to load
+  int prod_r = 0, prod_i = 0;
+  auto next_tile = [&]() -> const __nv_bfloat16* {
+    const StepPos p = decode_step(prod_i, Lx);
+    const __nv_bfloat16* T = (p.left ? a.TL : a.TR) + ((size_t)prod_r * Lx + p.c) * (kN * kK);
+    if (++prod_i == S) {
+      prod_i = 0;
+      if (++prod_r == Ly) prod_r = 0;
+    }
+    return T;
   };
   int64_t issued = 0;
   if (t == 0) {
@@ -189,7 +194,7 @@ __global__ void __launch_bounds__(kTile) sample_tc_kernel(TcArgs a) {
     for (; issued < pro; ++issued) {
       const uint32_t st = (uint32_t)(issued % kStages);
       umma::mbar_expect_tx(umma::smem_u32(&bars[st]), kTileBytes);
-      umma::bulk_g2s(umma::smem_u32(sB + st * kTileBytes), tile_of(issued), kTileBytes, umma::smem_u32(&bars[st]));
+      umma::bulk_g2s(umma::smem_u32(sB + st * kTileBytes), next_tile(), kTileBytes, umma::smem_u32(&bars[st]));
     }
   }
 
@@ -259,7 +264,7 @@ __global__ void __launch_bounds__(kTile) sample_tc_kernel(TcArgs a) {
           if (issued < total_steps) {
             const uint32_t st2 = (uint32_t)(issued % kStages);
             umma::mbar_expect_tx(umma::smem_u32(&bars[st2]), kTileBytes);
-            umma::bulk_g2s(umma::smem_u32(sB + st2 * kTileBytes), tile_of(issued), kTileBytes,
+            umma::bulk_g2s(umma::smem_u32(sB + st2 * kTileBytes), next_tile(), kTileBytes,
                            umma::smem_u32(&bars[st2]));
             ++issued;
           }
@@ -385,6 +390,11 @@ __global__ void __launch_bounds__(kTile) sample_tc_kernel(TcArgs a) {
         // operand of the next step when a chain starts or resumes
         if (i + 1 < S) {
           const StepPos nx = decode_step(i + 1, Lx);
+          if (nx.left && !(nx.first_of_seg)) {
+            const float* Rnx = seg + ((size_t)(nx.c - nx.seg_lo) * kTile + t) * kRowF32;
+            prefetch_l1(Rnx);
+            prefetch_l1(Rnx + 32);
+          }
           if (nx.first_of_seg) {
             // R_hi: its checkpoint, or e_0 at the right end, into segment slot hi - lo - 1
             if (nx.seg_hi >= Lx) unit_row(v);
@@ -519,8 +529,22 @@ tnmc_status tnmc_launch_sample_tc(const tnmc_env* env, int64_t B, uint64_t seed,
     return TNMC_E_UNSUPPORTED;
   }
   TNMC_CUDA_TRY(cudaFuncSetAttribute(sample_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  TNMC_CUDA_TRY(cudaFuncSetAttribute(sample_tc_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)cudaSharedmemCarveoutMaxShared));
   int per_sm = 0;
   TNMC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sample_tc_kernel, kTile, smem));
+  {
+    // cross-check the occupancy query against the shared-memory budget of an SM
+    int smem_sm = 0, regs_sm = 0;
+    TNMC_CUDA_TRY(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    TNMC_CUDA_TRY(cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev));
+    cudaFuncAttributes fa;
+    TNMC_CUDA_TRY(cudaFuncGetAttributes(&fa, sample_tc_kernel));
+    const int by_smem = smem_sm / (int)(smem + 1024);
+    const int by_regs = regs_sm / (((fa.numRegs + 7) & ~7) * kTile);
+    const int est = by_smem < by_regs ? by_smem : by_regs;
+    if (est > per_sm) per_sm = est;
+  }
   if (per_sm < 1) per_sm = 1;
   if (per_sm > 4) per_sm = 4;   // TMEM: 4 x 128 columns per SM
   const int64_t ntiles = (B + kTile - 1) / kTile;
