@@ -166,10 +166,17 @@ def round_bf16(x):
     return np.ldexp(np.round(np.ldexp(m, 8 + (np.frexp(x)[1] - e))), e - 8)
 
 
+def split_bf16(x):
+    """hi + lo with hi = bf16(x), lo = bf16(x - hi): x to about 16 significant bits."""
+    hi = round_bf16(x)
+    return hi + round_bf16(np.asarray(x, dtype=np.float64) - hi)
+
+
 def env_bf16(env):
-    """Copy of env whose tensors are rounded to bfloat16 (the BF16 contraction's operands)."""
+    """Copy of env with every tensor entry replaced by its BF16 hi + lo pair (the
+    operands of the tensor-core contraction)."""
     out = Env(env.Lx, env.Ly, env.beta, env.chi, env.Jh, env.Jv, env.h)
-    out.M = [[round_bf16(t) for t in row] for row in env.M]
+    out.M = [[split_bf16(t) for t in row] for row in env.M]
     out.log_scale, out.log_lambda, out.logZ = env.log_scale, env.log_lambda, env.logZ
     return out
 

@@ -17,9 +17,10 @@ constexpr int kMaxPad = 64;       // padded bond stride P <= 64
 //   M64   FP64 master, [Ly][Lx][P][2][P]  M[a][s][b]      (left layout)
 //   L{T}  sampler copy in precision T, same layout as M64
 //   R{T}  sampler copy in precision T, [Ly][Lx][P][P][2]  MT[b][a][s]
-//   L16 / R16 (BF16) instead hold the tensor-core operand tiles: per (r, c) a
-//         128 x 64 K-major 128-byte-swizzled tile (left: n = s*64 + b, k = a;
-//         right: n = s*64 + a, k = b), zero-padded to 64.
+//   L16 / R16 (BF16) instead hold the tensor-core operand tiles: per (r, c) two
+//         128 x 64 K-major 128-byte-swizzled tiles, hi = bf16(M) then
+//         lo = bf16(M - hi) (left: n = s*64 + b, k = a; right: n = s*64 + a, k = b),
+//         zero-padded to 64.
 //   fe    FP64 [Ly][Lx][2]: exp(-beta Jv[r-1][c]), exp(+beta Jv[r-1][c]); 1 for r = 0
 //   fe32  same in FP32
 // ---------------------------------------------------------------------------

@@ -32,8 +32,9 @@ constexpr int kTile = 128;          // samples per CTA (UMMA M)
 constexpr int kK = 64;              // padded bond dimension (UMMA K per site)
 constexpr int kN = 128;             // 2 x 64 outputs (UMMA N)
 constexpr int kKS = 8;              // checkpoint stride (sites)
-constexpr int kStages = 4;          // environment-tile ring
-constexpr uint32_t kTileBytes = kN * kK * 2;   // 16 KiB
+constexpr int kStages = 2;          // environment-tile ring (one step of look-ahead)
+constexpr uint32_t kTileBytes = kN * kK * 2;   // 16 KiB: one BF16 operand tile
+constexpr uint32_t kStageBytes = 2 * kTileBytes;   // hi + lo tiles of one (r, c)
 constexpr uint32_t kVecBytes = kTile * kK * 2;  // 16 KiB (one BF16 A operand)
 constexpr uint32_t kRowF32 = kK;                // floats per scratch row
 constexpr uint32_t kPollLimit = 1u << 24;
@@ -141,7 +142,7 @@ __global__ void __launch_bounds__(kTile, 2) sample_tc_kernel(TcArgs a) {
   unsigned char* sHi = base;
   unsigned char* sLo = base + kVecBytes;
   unsigned char* sB = base + 2 * kVecBytes;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + kStages * kTileBytes);   // full[kStages], mma
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + kStages * kStageBytes);  // full[kStages], mma
   uint32_t* misc = reinterpret_cast<uint32_t*>(bars + kStages + 1);         // [0] tmem base, [1] abort
   const int Lx = a.e.Lx, Ly = a.e.Ly;
   const int W = (Lx + 31) >> 5;
@@ -181,7 +182,7 @@ __global__ void __launch_bounds__(kTile, 2) sample_tc_kernel(TcArgs a) {
   int prod_r = 0, prod_i = 0;
   auto next_tile = [&]() -> const __nv_bfloat16* {
     const StepPos p = decode_step(prod_i, Lx);
-    const __nv_bfloat16* T = (p.left ? a.TL : a.TR) + ((size_t)prod_r * Lx + p.c) * (kN * kK);
+    const __nv_bfloat16* T = (p.left ? a.TL : a.TR) + ((size_t)prod_r * Lx + p.c) * (2 * kN * kK);
     if (++prod_i == S) {
       prod_i = 0;
       if (++prod_r == Ly) prod_r = 0;
@@ -193,8 +194,8 @@ __global__ void __launch_bounds__(kTile, 2) sample_tc_kernel(TcArgs a) {
     const int64_t pro = total_steps < kStages - 1 ? total_steps : (int64_t)(kStages - 1);
     for (; issued < pro; ++issued) {
       const uint32_t st = (uint32_t)(issued % kStages);
-      umma::mbar_expect_tx(umma::smem_u32(&bars[st]), kTileBytes);
-      umma::bulk_g2s(umma::smem_u32(sB + st * kTileBytes), next_tile(), kTileBytes, umma::smem_u32(&bars[st]));
+      umma::mbar_expect_tx(umma::smem_u32(&bars[st]), kStageBytes);
+      umma::bulk_g2s(umma::smem_u32(sB + st * kStageBytes), next_tile(), kStageBytes, umma::smem_u32(&bars[st]));
     }
   }
 
@@ -254,17 +255,21 @@ __global__ void __launch_bounds__(kTile, 2) sample_tc_kernel(TcArgs a) {
           } else {
             const uint64_t ah = umma::sw128_desc(umma::smem_u32(sHi));
             const uint64_t al = umma::sw128_desc(umma::smem_u32(sLo));
-            const uint64_t bd = umma::sw128_desc(umma::smem_u32(sB + st * kTileBytes));
+            const uint64_t bh = umma::sw128_desc(umma::smem_u32(sB + st * kStageBytes));
+            const uint64_t bl = umma::sw128_desc(umma::smem_u32(sB + st * kStageBytes + kTileBytes));
+            // (A_hi + A_lo)(B_hi + B_lo) without the A_lo B_lo term (below 2^-16 relative)
 #pragma unroll
-            for (int k = 0; k < kK / 16; ++k) umma::mma_bf16(tmem, ah + 2 * k, bd + 2 * k, idesc, k > 0);
+            for (int k = 0; k < kK / 16; ++k) umma::mma_bf16(tmem, ah + 2 * k, bh + 2 * k, idesc, k > 0);
 #pragma unroll
-            for (int k = 0; k < kK / 16; ++k) umma::mma_bf16(tmem, al + 2 * k, bd + 2 * k, idesc, 1);
+            for (int k = 0; k < kK / 16; ++k) umma::mma_bf16(tmem, al + 2 * k, bh + 2 * k, idesc, 1);
+#pragma unroll
+            for (int k = 0; k < kK / 16; ++k) umma::mma_bf16(tmem, ah + 2 * k, bl + 2 * k, idesc, 1);
           }
           umma::mma_commit(umma::smem_u32(&bars[kStages]));
           if (issued < total_steps) {
             const uint32_t st2 = (uint32_t)(issued % kStages);
-            umma::mbar_expect_tx(umma::smem_u32(&bars[st2]), kTileBytes);
-            umma::bulk_g2s(umma::smem_u32(sB + st2 * kTileBytes), next_tile(), kTileBytes,
+            umma::mbar_expect_tx(umma::smem_u32(&bars[st2]), kStageBytes);
+            umma::bulk_g2s(umma::smem_u32(sB + st2 * kStageBytes), next_tile(), kStageBytes,
                            umma::smem_u32(&bars[st2]));
             ++issued;
           }
@@ -475,9 +480,13 @@ __global__ void derive_tc_kernel(DeviceEnv e, __nv_bfloat16* TR, __nv_bfloat16* 
     // right tile: a = x, b = k ; left tile: b = x, a = k
     const double vr = (x < P && k < P) ? M[((size_t)x * 2 + s) * P + k] : 0.0;
     const double vl = (x < P && k < P) ? M[((size_t)k * 2 + s) * P + x] : 0.0;
-    const size_t off = tt * per + umma::sw128_offset(nn, k) / 2;
-    TR[off] = __double2bfloat16(vr);
-    TL[off] = __double2bfloat16(vl);
+    // hi = bf16(v), lo = bf16(v - hi): the pair carries about 16 significant bits
+    const size_t off = tt * 2 * per + umma::sw128_offset(nn, k) / 2;
+    const __nv_bfloat16 rh = __double2bfloat16(vr), lh = __double2bfloat16(vl);
+    TR[off] = rh;
+    TR[off + per] = __double2bfloat16(vr - (double)__bfloat162float(rh));
+    TL[off] = lh;
+    TL[off + per] = __double2bfloat16(vl - (double)__bfloat162float(lh));
   }
 }
 
@@ -494,7 +503,7 @@ __global__ void couplings32_kernel(DeviceEnv e, float* h32, float* Jh32, float* 
 }  // namespace
 }  // namespace tnmc
 
-size_t tnmc_tc_tile_bytes() { return tnmc::kTileBytes; }
+size_t tnmc_tc_tile_bytes() { return tnmc::kStageBytes; }
 
 tnmc_status tnmc_launch_derive_tc(tnmc_env* env, cudaStream_t stream) {
   using namespace tnmc;
@@ -518,7 +527,7 @@ tnmc_status tnmc_launch_sample_tc(const tnmc_env* env, int64_t B, uint64_t seed,
     return TNMC_E_UNSUPPORTED;
   }
   const int W = (d.Lx + 31) / 32;
-  const size_t smem = 1024 + 2 * kVecBytes + kStages * kTileBytes + (kStages + 1) * 8 + 16 +
+  const size_t smem = 1024 + 2 * kVecBytes + kStages * kStageBytes + (kStages + 1) * 8 + 16 +
                       (size_t)2 * W * kTile * sizeof(uint32_t) + (size_t)5 * d.Lx * sizeof(float);
   int dev = 0, nsm = 0, max_optin = 0;
   TNMC_CUDA_TRY(cudaGetDevice(&dev));
