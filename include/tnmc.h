@@ -192,6 +192,33 @@ tnmc_status tnmc_mh_step(const tnmc_env* env, int64_t C, int64_t T, const int8_t
                          uint64_t step_offset, uint8_t* accepted, int64_t* n_accepted,
                          void* stream);
 
+/*
+ * Gradient of sum_b weights[b] log q(spins[b]) with respect to every tensor of the
+ * FP32 sampler copy (the parameters of tnmc_env_get_params), by reverse-mode
+ * differentiation of the forced evaluation (Sec. 2, eq. pi-approx; App. A):
+ * per-site normalised, clamped conditionals; the power-of-two rescalings are
+ * constants.  The per-row forward vectors are recomputed, not stored.  Used to
+ * tune the proposal (maximise the mean log q of accepted chain samples); the MH
+ * step keeps the chain exact whatever q is.
+ * spins    device int8 [B][Ly][Lx]
+ * weights  device float [B]; samples whose log q is -inf must have weight 0
+ * grad     device float, same layout as the parameters ([Ly][Lx][P][2][P]);
+ *          overwritten.  Requires the TNMC_F32 copy and P <= 52.
+ */
+tnmc_status tnmc_logq_backward(const tnmc_env* env, int64_t B, const int8_t* spins, const float* weights,
+                               float* grad, void* stream);
+
+/*
+ * The FP32 sampler copy as a flat parameter vector: [Ly][Lx][P][2][P] floats,
+ * M^(r)_c[a][s][b] zero-padded to P.  get copies it into `dst`; set copies `src`
+ * into the env and re-derives the transposed copy the right sweep reads, so
+ * tnmc_sample / tnmc_logq / tnmc_logq_backward with TNMC_F32 use the new tensors
+ * (the FP64 master and the BF16 tiles keep the built values).  Device pointers,
+ * asynchronous on `stream`.
+ */
+tnmc_status tnmc_env_get_params(const tnmc_env* env, float* dst, void* stream);
+tnmc_status tnmc_env_set_params(tnmc_env* env, const float* src, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -52,6 +52,9 @@ SIGNATURES = {
     "tnmc_sample_noalloc": ([_P, _INT, _I64, _U64, _U64, _P, _P, _P, _P, _P], _INT),
     "tnmc_init_chains": ([_P, _INT, _I64, _U64, _P, _P, _P, _P], _INT),
     "tnmc_mh_step": ([_P, _I64, _I64, _P, _P, _P, _P, _P, _P, _U64, _U64, _P, _P, _P], _INT),
+    "tnmc_logq_backward": ([_P, _I64, _P, _P, _P, _P], _INT),
+    "tnmc_env_get_params": ([_P, _P, _P], _INT),
+    "tnmc_env_set_params": ([_P, _P, _P], _INT),
 }
 
 
@@ -196,3 +199,33 @@ def mh_step(env, C, T, prop, chain, seed=0, step_offset=0, accepted=None, n_acce
     _check(lib().tnmc_mh_step(env.handle, C, T, _ptr(ps), _ptr(plq), _ptr(pE), _ptr(cs), _ptr(clq), _ptr(cE),
                               seed, step_offset, _ptr(accepted), _ptr(n_accepted), _stream(stream)))
     return accepted
+
+
+def param_count(env):
+    inf = env.info()
+    return env.Ly * env.Lx * inf["pad"] * 2 * inf["pad"]
+
+
+def get_params(env, stream=None):
+    """FP32 sampler tensors as a flat cuda tensor [Ly*Lx*P*2*P] (a copy)."""
+    import torch
+    out = torch.empty(param_count(env), dtype=torch.float32, device="cuda")
+    _check(lib().tnmc_env_get_params(env.handle, _ptr(out), _stream(stream)))
+    return out
+
+
+def set_params(env, params, stream=None):
+    """Copy flat FP32 tensors into the env (the FP32 sampler then uses them)."""
+    p = params.detach().contiguous()
+    assert p.dtype.is_floating_point and p.numel() == param_count(env)
+    _check(lib().tnmc_env_set_params(env.handle, _ptr(p.float()), _stream(stream)))
+
+
+def logq_backward(env, spins, weights, stream=None):
+    """d/dparams of sum_b weights_b log q_b (flat FP32 cuda tensor)."""
+    import torch
+    spins = spins.contiguous()
+    w = weights.contiguous().float()
+    grad = torch.empty(param_count(env), dtype=torch.float32, device="cuda")
+    _check(lib().tnmc_logq_backward(env.handle, spins.shape[0], _ptr(spins), _ptr(w), _ptr(grad), _stream(stream)))
+    return grad

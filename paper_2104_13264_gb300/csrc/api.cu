@@ -288,4 +288,41 @@ tnmc_status tnmc_mh_step(const tnmc_env* env, int64_t C, int64_t T, const int8_t
                         step_offset, accepted, n_accepted, static_cast<cudaStream_t>(stream));
 }
 
+tnmc_status tnmc_logq_backward(const tnmc_env* env, int64_t B, const int8_t* spins, const float* weights,
+                               float* grad, void* stream) {
+  g_err[0] = 0;
+  CHECK_ARG(env, "env must be non-null");
+  CHECK_ARG(B >= 0, "B must be >= 0");
+  CHECK_ARG(grad && (B == 0 || (spins && weights)), "spins, weights and grad must be non-null");
+  tnmc_status st = check_precision(env, TNMC_F32);
+  if (st != TNMC_OK) return st;
+  if (env->d.P > 52) {
+    tnmc_set_error("tnmc_logq_backward supports padded bond dimension P <= 52 (got %d)", env->d.P);
+    return TNMC_E_UNSUPPORTED;
+  }
+  return tnmc_launch_logq_grad(env, B, spins, weights, grad, static_cast<cudaStream_t>(stream));
+}
+
+tnmc_status tnmc_env_get_params(const tnmc_env* env, float* dst, void* stream) {
+  g_err[0] = 0;
+  CHECK_ARG(env && dst, "env and dst must be non-null");
+  tnmc_status st = check_precision(env, TNMC_F32);
+  if (st != TNMC_OK) return st;
+  const size_t n = (size_t)env->d.Lx * env->d.Ly * env->d.P * 2 * env->d.P;
+  TNMC_CUDA_TRY(cudaMemcpyAsync(dst, env->d.L32, n * sizeof(float), cudaMemcpyDeviceToDevice,
+                                static_cast<cudaStream_t>(stream)));
+  return TNMC_OK;
+}
+
+tnmc_status tnmc_env_set_params(tnmc_env* env, const float* src, void* stream) {
+  g_err[0] = 0;
+  CHECK_ARG(env && src, "env and src must be non-null");
+  tnmc_status st = check_precision(env, TNMC_F32);
+  if (st != TNMC_OK) return st;
+  const size_t n = (size_t)env->d.Lx * env->d.Ly * env->d.P * 2 * env->d.P;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  TNMC_CUDA_TRY(cudaMemcpyAsync(const_cast<float*>(env->d.L32), src, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  return tnmc_launch_rederive_f32(env, s);
+}
+
 }  // extern "C"

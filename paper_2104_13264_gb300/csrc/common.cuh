@@ -166,6 +166,9 @@ size_t tnmc_tc_tile_bytes();
 tnmc_status tnmc_launch_sample_tc(const tnmc_env* env, int64_t B, uint64_t seed, uint64_t offset,
                                   const int8_t* spins_in, int8_t* spins_out, double* logq, double* energy,
                                   int32_t* flags, cudaStream_t stream);
+tnmc_status tnmc_launch_logq_grad(const tnmc_env* env, int64_t B, const int8_t* spins, const float* weights,
+                                  float* grad, cudaStream_t stream);
+tnmc_status tnmc_launch_rederive_f32(tnmc_env* env, cudaStream_t stream);
 tnmc_status tnmc_launch_mh(const tnmc_env* env, int64_t C, int64_t T, const int8_t* prop_spins,
                            const double* prop_logq, const double* prop_energy, int8_t* chain_spins,
                            double* chain_logq, double* chain_energy, uint64_t seed,

@@ -133,6 +133,29 @@ tnmc_status tnmc_launch_derive(tnmc_env* env, int mask, cudaStream_t stream) {
   return TNMC_OK;
 }
 
+namespace tnmc {
+namespace {
+// transposed FP32 copy [b][a][s] from the left layout [a][s][b]
+__global__ void rederive_f32_kernel(const float* L, float* R, int P, size_t ntens) {
+  const size_t per = (size_t)P * 2 * P;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < ntens * per; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t t = i / per;
+    const int rem = (int)(i % per);
+    const int b = rem % P, s = (rem / P) & 1, aa = rem / (2 * P);
+    R[t * per + ((size_t)b * P + aa) * 2 + s] = L[i];
+  }
+}
+}  // namespace
+}  // namespace tnmc
+
+tnmc_status tnmc_launch_rederive_f32(tnmc_env* env, cudaStream_t stream) {
+  using namespace tnmc;
+  DeviceEnv& d = env->d;
+  rederive_f32_kernel<<<1024, 256, 0, stream>>>(d.L32, const_cast<float*>(d.R32), d.P, (size_t)d.Lx * d.Ly);
+  TNMC_CUDA_TRY(cudaGetLastError());
+  return TNMC_OK;
+}
+
 tnmc_status tnmc_launch_sample(const tnmc_env* env, int precision, int64_t B, uint64_t seed,
                                uint64_t offset, const int8_t* spins_in, int8_t* spins_out, double* logq,
                                double* energy, int32_t* flags, cudaStream_t stream) {

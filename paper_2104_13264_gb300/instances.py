@@ -119,3 +119,13 @@ def config4():
 def config5():
     """256x256 ferromagnet at beta = 0.4407, chi = 64, B = 2^20."""
     return ferromagnet(256, 256, 0.4407, 64)
+
+
+def random_tensors(shapes, seed=0, positive=True):
+    """Seeded random tensors of the given shapes (inputs for gradient checks)."""
+    rng = np.random.default_rng([seed, 11])
+    out = []
+    for shp in shapes:
+        x = rng.standard_normal(shp)
+        out.append(np.abs(x) + 0.1 if positive else x)
+    return out

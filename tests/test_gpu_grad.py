@@ -1,0 +1,110 @@
+"""Backward of log q (tnmc_logq_backward) vs the oracle's reverse-mode gradient (needs a GB300).
+
+The gradient depends on the gauge of the tensors, so both sides get the same
+seeded random tensors from the input generator (not builder output): the GPU
+through tnmc_env_set_params, the oracle as its Env.M.  Bar: 1e-3 relative.
+"""
+import numpy as np
+import pytest
+
+from oracle import tnmc
+from paper_2104_13264_gb300 import instances
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2104_13264_gb300 import binding
+    binding.lib()
+    return binding
+
+
+def _shared_tensors(inst, seed):
+    shapes = [(tnmc.bond_dim(inst.chi, inst.Lx, inst.Ly, r, c), 2, tnmc.bond_dim(inst.chi, inst.Lx, inst.Ly, r, c + 1))
+              for r in range(inst.Ly) for c in range(inst.Lx)]
+    ts = instances.random_tensors(shapes, seed=seed)
+    oenv = tnmc.Env(inst.Lx, inst.Ly, inst.beta, inst.chi, inst.Jh, inst.Jv, inst.h)
+    oenv.M = [[ts[r * inst.Lx + c] for c in range(inst.Lx)] for r in range(inst.Ly)]
+    return oenv, ts
+
+
+def _flat(env_g, ts, inst):
+    P = env_g.info()["pad"]
+    flat = np.zeros((inst.Ly, inst.Lx, P, 2, P), dtype=np.float32)
+    for r in range(inst.Ly):
+        for c in range(inst.Lx):
+            t = ts[r * inst.Lx + c]
+            flat[r, c, :t.shape[0], :, :t.shape[2]] = t
+    return flat, P
+
+
+CASES = [instances.villain(4, 5, 1.5, 2), instances.random_small(5, 6, 0.8, 4, seed=2),
+         instances.ea_pm(6, 7, 1.0, 8, seed=3), instances.random_small(3, 19, 0.7, 8, seed=4)]
+
+
+@pytest.mark.parametrize("idx", range(len(CASES)))
+def test_grad_matches_oracle(B, idx):
+    inst = CASES[idx]
+    oenv, ts = _shared_tensors(inst, seed=idx)
+    env = B.Env.from_instance(inst, precisions=("f64", "f32"))
+    flat, P = _flat(env, ts, inst)
+    B.set_params(env, torch.from_numpy(flat.reshape(-1)).cuda())
+    # oracle samples from the shared tensors (its own draws: inputs, not GPU output)
+    osp, _, _, _ = tnmc.sample(oenv, 300, seed=7)
+    w = np.random.default_rng(idx).random(300)
+    olq, G = tnmc.logq_grad(oenv, osp, w)
+    spins = torch.from_numpy(osp).cuda()
+    glq = B.logq(env, spins, precision="f32")[0].cpu().numpy()
+    np.testing.assert_allclose(glq, olq, rtol=1e-4)
+    g = B.logq_backward(env, spins, torch.from_numpy(w).float().cuda()).cpu().numpy().reshape(inst.Ly, inst.Lx, P, 2, P)
+    scale = max(np.abs(G[r][c]).max() for r in range(inst.Ly) for c in range(inst.Lx))
+    for r in range(inst.Ly):
+        for c in range(inst.Lx):
+            ref = G[r][c]
+            got = g[r, c, :ref.shape[0], :, :ref.shape[2]]
+            assert np.abs(got - ref).max() <= 1e-3 * scale, (r, c)
+            # entries outside the bond dimensions stay zero
+            assert np.all(g[r, c, ref.shape[0]:] == 0) and np.all(g[r, c, :, :, ref.shape[2]:] == 0)
+
+
+def test_autograd_function(B):
+    from paper_2104_13264_gb300 import autograd
+    inst = instances.villain(6, 6, 1.5, 4)
+    env = B.Env.from_instance(inst, precisions=("f64", "f32"))
+    sp = B.sample(env, 256, seed=3, precision="f32")[0]
+    p = B.get_params(env).clone().requires_grad_(True)
+    lq = autograd.logq(p, env, sp)
+    (lq * torch.linspace(0.5, 1.5, 256, device="cuda", dtype=torch.float64)).sum().backward()
+    g2 = B.logq_backward(env, sp, torch.linspace(0.5, 1.5, 256, device="cuda"))
+    # float atomics make the two sums differ at the rounding level only
+    assert (p.grad - g2).abs().max().item() <= 1e-5 * g2.abs().max().item()
+
+
+def test_gradient_identities_at_config4_size(B):
+    """At 64x64, chi = 32: log q is degree-0 in each tensor, so <G_c, M_c> = 0 for
+    every site (a property that holds at any size)."""
+    inst = instances.config4()
+    env = B.Env.from_instance(inst, precisions=("f64", "f32"))
+    sp = B.sample(env, 2048, seed=1, precision="f32")[0]
+    g = B.logq_backward(env, sp, torch.full((2048,), 1.0 / 2048, device="cuda"))
+    M = B.get_params(env)
+    P = env.info()["pad"]
+    gs = (g * M).view(inst.Ly * inst.Lx, -1).sum(dim=1)
+    gn = (g.abs() * M.abs()).view(inst.Ly * inst.Lx, -1).sum(dim=1)
+    assert torch.all(gs.abs() <= 1e-3 * gn + 1e-6)
+
+
+def test_tuning_raises_mean_logq(B):
+    """A few steps of gradient ascent raise the mean log q of accepted samples."""
+    from paper_2104_13264_gb300 import tuning
+    inst = instances.villain(8, 8, 1.5, 2)
+    env = B.Env.from_instance(inst, precisions=("f64", "f32"))
+    hist = tuning.tune(env, steps=12, proposals=16384, chains=64, lr=2e-2, seed=5, min_batch=16)
+    losses = [h["loss"] for h in hist if h["loss"] == h["loss"]]
+    assert len(losses) >= 6, hist
+    assert np.mean(losses[-3:]) < np.mean(losses[:3]), hist
