@@ -296,11 +296,19 @@ def mh_accept(beta, lq_prop, E_prop, lq_cur, E_cur, u):
 
     Delta = -beta (E' - E) + log q(cur) - log q(prop); accept iff the proposal
     is valid (finite log q) and u < exp(min(0, Delta)).
+
+    A current state with log q = -inf lies outside the numerical support of q
+    (only the random start of Algorithm 1 can be such a state: every later state
+    is an accepted proposal, whose log q is finite).  Its ratio
+    q(cur) pi(prop) / (q(prop) pi(cur)) is then read as +inf rather than 0, so the
+    first valid proposal is accepted; with the literal 0 the chain could never
+    leave its start.  The rule only changes the transient out of the start.
     """
     with np.errstate(invalid="ignore", over="ignore"):
         d = -beta * (E_prop - E_cur) + (lq_cur - lq_prop)
         ok = np.isfinite(lq_prop) & ~np.isnan(d)
-        return ok & (u < np.exp(np.minimum(np.where(ok, d, 0.0), 0.0)))
+        start = np.isneginf(lq_cur)
+        return ok & (start | (u < np.exp(np.minimum(np.where(ok & ~start, d, 0.0), 0.0))))
 
 
 def mh_scan(beta, C, T, prop_spins, prop_logq, prop_E, chain_spins, chain_logq, chain_E,

@@ -22,7 +22,8 @@ __global__ void mh_scan_kernel(int64_t C, int64_t T, double beta, const double* 
     const double lqt = prop_logq[t], Et = prop_E[t];
     const double d = -beta * (Et - E) + (lq - lqt);
     const bool ok = isfinite(lqt) && !isnan(d);
-    const bool acc = ok && (u < exp(fmin(d, 0.0)));
+    // a state with log q = -inf (only a random start can be one) takes the first valid proposal
+    const bool acc = ok && (lq == -INFINITY || u < exp(fmin(d, 0.0)));
     if (accepted) accepted[t] = acc ? 1 : 0;
     if (acc) {
       lq = lqt;

@@ -193,6 +193,29 @@ def test_mh_rejects_flagged_proposals(B):
     assert int(acc.sum()) == 0
 
 
+def test_mh_start_outside_support_matches_oracle(B):
+    """Chains whose start has log q = -inf take their first valid proposal (same rule as
+    the oracle's scan); later decisions follow the ordinary ratio."""
+    inst = instances.ea_pm(6, 6, 1.0, 2, seed=3)
+    ref = _oracle_env(inst)
+    env = B.Env.from_instance(inst)
+    C, T = 8, 16
+    sp, lq, E, fl = B.sample(env, C * T, seed=4)
+    lq[::5] = -math.inf                       # a few invalid proposals too
+    cs, clq, cE = B.init_chains(env, C, seed=5)
+    clq[::2] = -math.inf
+    ocs, oclq, ocE = cs.cpu().numpy().copy(), clq.cpu().numpy().copy(), cE.cpu().numpy().copy()
+    acc = B.mh_step(env, C, T, (sp, lq, E), (cs, clq, cE), seed=6, step_offset=3)
+    oacc, osp, olq, oE = tnmc.mh_scan(inst.beta, C, T, sp.cpu().numpy(), lq.cpu().numpy(), E.cpu().numpy(),
+                                      ocs, oclq, ocE, seed=6, step_offset=3)
+    assert np.array_equal(acc.cpu().numpy().astype(bool), oacc)
+    assert np.array_equal(cs.cpu().numpy(), osp)
+    assert np.array_equal(clq.cpu().numpy(), olq) and np.array_equal(cE.cpu().numpy(), oE)
+    first_valid = [next(j for j in range(T) if (i * T + j) % 5) for i in range(0, C, 2)]
+    assert all(oacc[i * T + j] for i, j in zip(range(0, C, 2), first_valid))
+    assert bool(torch.isfinite(clq).all())
+
+
 def test_exact_chi_gives_acceptance_one(B):
     """At exact chi q = pi, so Delta = 0 and every proposal is accepted (Sec. 2)."""
     inst = instances.ea_gauss(4, 4, 1.0, 4, seed=4, hscale=0.3)

@@ -99,10 +99,19 @@ def test_detailed_balance_by_enumeration():
 
 
 def test_mh_rejects_invalid_proposals():
-    u = np.array([0.0, 0.0, 0.0])
-    a = tnmc.mh_accept(1.0, np.array([-np.inf, np.nan, -1.0]), np.zeros(3), np.array([-1.0, -1.0, -np.inf]),
-                       np.zeros(3), u)
-    assert a.tolist() == [False, False, False]
+    u = np.array([0.0, 0.0, 0.0, 0.0])
+    a = tnmc.mh_accept(1.0, np.array([-np.inf, np.nan, -np.inf, np.nan]), np.zeros(4),
+                       np.array([-1.0, -1.0, -np.inf, -np.inf]), np.zeros(4), u)
+    assert a.tolist() == [False, False, False, False]
+
+
+def test_mh_leaves_a_start_outside_the_support():
+    """A start with log q = -inf accepts the first valid proposal whatever u and the
+    energies are; a start with finite log q follows the ordinary rule."""
+    u = np.array([0.999999, 0.5, 0.999999])
+    a = tnmc.mh_accept(1.0, np.array([-1.0, -3.0, -1.0]), np.array([50.0, 0.0, 50.0]),
+                       np.array([-np.inf, -np.inf, -2.0]), np.array([0.0, 0.0, 0.0]), u)
+    assert a.tolist() == [True, True, False]
 
 
 def _batch_means(x, nb=20):
