@@ -28,6 +28,8 @@ CONFIGS = {
     # name: (instance factory, B, chains C, default precision, description)
     "c1": ("config1", 10000, 1, "f64", "8x8 ferromagnet, beta=0.44, chi=8, 10^4 proposals, 1 chain"),
     "c2": ("config2", 65536, 256, "f32", "32x32 +-J EA, beta=1.0, chi=16, B=65536"),
+    "c3": ("config3", 4096, 16, "f32", "256 Gaussian EA instances, L in {16,24,32,48,64}, chi in {8,16,32}, "
+                                       "beta=2.0, 4096 proposals each, one persistent graph-captured launch"),
     "c4": ("config4", 16384, 64, "f32", "64x64 fully frustrated, beta=1.5, chi=32, B=16384"),
     "c5": ("config5", 1 << 20, 1024, "bf16", "256x256 ferromagnet, beta=0.4407, chi=64, B=2^20"),
 }
@@ -309,6 +311,193 @@ def run_tnmc(args):
         pg.destroy_process_group()
 
 
+def run_batched(args):
+    """The batched persistent form: every instance's proposals in one persistent launch,
+    the MH scan of every chain in one launch, both replayed from a captured CUDA graph;
+    tiles and item order from the autotuner.  Timed region: K graph replays."""
+    import torch
+    from paper_2104_13264_gb300 import batched
+    from paper_2104_13264_gb300 import binding as Bd
+    from paper_2104_13264_gb300 import instances
+
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+    fac, Bdef, Cdef, pdef, desc = CONFIGS["c3"]
+    insts = instances.config3()
+    B = args.batch or Bdef
+    C = args.chains or Cdef
+    prec = args.precision or pdef
+    dev = torch.device("cuda", local)
+    t0 = time.time()
+    envs = Bd.build_envs_batched(insts, precisions=tuple(sorted({"f64", prec})))
+    statuses = [e.status() for e in envs]
+    env_build_s = time.time() - t0
+    t0 = time.time()
+    run = batched.BatchRunner(envs, B, chains=C, precision=prec, seed=args.seed + 7919 * rank)
+    tune_s = time.time() - t0
+    plan = run.plan
+    binf = plan.info()
+    stream = torch.cuda.current_stream()
+    run.capture()
+    for _ in range(args.warmup):
+        run.step()
+    torch.cuda.synchronize()
+    run.n_accepted.zero_()
+    # one timed kernel-only launch of the persistent sampler for the roofline
+    k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for i in range(args.steps):
+        run.step()
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    n_accepted = int(run.n_accepted.sum().item())
+    props = binf["proposal_rows"]
+    # kernel time of the persistent sampler alone (same launch, eager, events on its stream)
+    ks = []
+    for i in range(max(1, args.steps)):
+        k0.record(stream)
+        plan.sample(run.prop, stream=stream)
+        k1.record(stream)
+        torch.cuda.synchronize()
+        ks.append(k0.elapsed_time(k1))
+    kern_s = statistics.mean(ks) / 1e3
+    if pg:
+        t = torch.tensor([total_ms, float(n_accepted)], dtype=torch.float64, device=dev)
+        mx = t.clone()
+        pg.all_reduce(mx, op=pg.ReduceOp.MAX)
+        sm = t.clone()
+        pg.all_reduce(sm, op=pg.ReduceOp.SUM)
+        total_ms, n_accepted = float(mx[0]), int(sm[1])
+
+    # end to end: chain states of every instance uploaded from pinned host memory before,
+    # and read back with the accept flags after, each graph replay
+    hs = torch.empty_like(run.chain[0], device="cpu").pin_memory()
+    hlq = torch.empty_like(run.chain[1], device="cpu").pin_memory()
+    hE = torch.empty_like(run.chain[2], device="cpu").pin_memory()
+    hacc = torch.empty_like(run.accepted, device="cpu").pin_memory()
+    hs.copy_(run.chain[0]); hlq.copy_(run.chain[1]); hE.copy_(run.chain[2])
+    nacc0 = int(run.n_accepted.sum().item())
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_steps = max(1, min(args.steps, 5))
+    e0.record(stream)
+    for i in range(e2e_steps):
+        run.chain[0].copy_(hs, non_blocking=True); run.chain[1].copy_(hlq, non_blocking=True)
+        run.chain[2].copy_(hE, non_blocking=True)
+        run.step()
+        hs.copy_(run.chain[0], non_blocking=True); hlq.copy_(run.chain[1], non_blocking=True)
+        hE.copy_(run.chain[2], non_blocking=True); hacc.copy_(run.accepted, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    e2e_acc = int(run.n_accepted.sum().item()) - nacc0
+    h2d = hs.numel() + 16 * binf["chain_rows"]
+    d2h = h2d + props
+
+    plain = None
+    if world == 1 and not args.no_plain:
+        plain = plain_batched_f64(Bd, envs, insts, B, C, args, stream)
+    if rank != 0:
+        if pg:
+            pg.destroy_process_group()
+        return
+    flops = sum(algorithmic_flops(inst) for inst in insts) * B
+    peaks, peak_src = load_peaks()
+    smmax = float(peaks.get("sm_max_mhz", 2070.0))
+    achieved_tf = flops / kern_s / 1e12
+    if prec == "f32":
+        peak = 152 * 128 * 2 * smmax * 1e6 / 1e12
+        psrc = "FP32 FFMA: 152 SM x 128 lanes x 2 x %.0f MHz" % smmax
+    else:
+        peak, psrc = 1.25, "FP64 nominal 1.25 TFLOP/s"
+    roof = {"bound": "alu", "unit": "TFLOP/s", "achieved": round(achieved_tf, 3), "peak": round(peak, 3),
+            "frac": round(achieved_tf / peak, 5), "traffic": None, "kernel": "sample_batched_kernel",
+            "kernel_ms": round(kern_s * 1e3, 3), "flop_per_launch": flops, "peak_source": psrc}
+    step_ms = total_ms / args.steps
+    acc_rate = n_accepted / (props * world * args.steps)
+    value = n_accepted / (total_ms / 1e3)
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline("c3", prec, args.cpu_seconds)
+        if cpu is not None and cpu.get("value") is not None:
+            cpu["value"] = cpu["value"] * acc_rate
+            cpu["unit"] = "accepted samples/s"
+    line = {
+        "metric": "accepted samples/s (TNMH proposals + MH, %s)" % desc,
+        "value": round(value, 3), "unit": "accepted samples/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(step_ms, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic (seeded instance generator)",
+        "config": {"workload": "c3", "description": desc, "instances": len(insts), "B_per_instance": B,
+                   "chains_per_instance": C, "precision": prec, "tile": plan.tile, "order": plan.order,
+                   "grid": binf["grid"], "parallelism": "replicas%d" % world,
+                   "l2": "outputs %.0f MB per step (spins + log q + energy)" % ((binf["proposal_bytes"] + 20 * props) / 1e6)},
+        "proposals_per_s": round(props * world / (step_ms / 1e3), 3), "acceptance": round(acc_rate, 5),
+        "flagged_fraction": float((run.prop[3] != 0).double().mean().item()),
+        "env_build_s": round(env_build_s, 3), "autotune_s": round(tune_s, 3),
+        "device_status_nonzero": sum(1 for s in statuses if s),
+        "roofline": roof, "cpu_baseline": cpu, "plain_f64": plain,
+        "e2e": {"value": round(e2e_acc / (e2e_ms * e2e_steps / 1e3), 3) if e2e_ms > 0 else None,
+                "unit": "accepted samples/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "ms_per_step": round(e2e_ms, 3)},
+        "gpu_launches": 5 * args.steps,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+
+
+def plain_batched_f64(Bd, envs, insts, B, C, args, stream):
+    """The plain FP64 form of the batched workload: one tnmc_sample + tnmc_mh_step per
+    instance, FP64, no graph, default tiles."""
+    import torch
+    dev = torch.device("cuda")
+    T = B // C
+    outs = (torch.empty(B * max(e.Lx * e.Ly for e in envs), dtype=torch.int8, device=dev),
+            torch.empty(B, dtype=torch.float64, device=dev), torch.empty(B, dtype=torch.float64, device=dev),
+            torch.empty(B, dtype=torch.int32, device=dev))
+    chains = [Bd.init_chains(e, C, seed=args.seed + 3, precision="f64") for e in envs]
+    nacc = torch.zeros(1, dtype=torch.int64, device=dev)
+
+    def one_pass(k):
+        for i, e in enumerate(envs):
+            sp = outs[0][:B * e.Lx * e.Ly].view(B, e.Ly, e.Lx)
+            Bd.sample(e, B, seed=args.seed, sample_offset=(i << 40) + k * B, precision="f64",
+                      out=(sp, outs[1], outs[2], outs[3]), stream=stream)
+            Bd.mh_step(e, C, T, (sp, outs[1], outs[2]), chains[i], seed=args.seed + 5, step_offset=(i << 40) + k * T,
+                       n_accepted=nacc, stream=stream)
+
+    one_pass(0)
+    torch.cuda.synchronize()
+    nacc.zero_()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    one_pass(1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) / 1e3
+    acc = int(nacc.item())
+    n = B * len(envs)
+    return {"proposals": n, "chains": C * len(envs), "proposals_per_s": round(n / sec, 3),
+            "accepted_per_s": round(acc / sec, 3), "acceptance": round(acc / n, 5), "seconds": round(sec, 3)}
+
+
 def plain_f64_form(Bd, env, inst, args, dev, stream):
     """The plain FP64 SIMT form on a bounded subset of the same workload: proposals/s,
     and accepted samples/s with its own MH scan (chains of the same length T)."""
@@ -347,9 +536,26 @@ def _oracle_workload(config, n_rows_cap):
     from paper_2104_13264_gb300 import instances
     fac = CONFIGS[config][0]
     inst = getattr(instances, fac)()
+    if config == "c3":
+        # a cost-weighted sample: one of the largest instances (L = 64, chi = 32) stands for
+        # the mean by the ratio of algorithmic work, applied by the caller
+        insts = inst
+        big = max(insts, key=lambda i: algorithmic_flops(i))
+        rows = min(big.Ly, n_rows_cap)
+        rng = np.random.default_rng(0)
+        env = tnmc.Env(big.Lx, rows, big.beta, big.chi, big.Jh[:rows], big.Jv[:rows - 1], big.h[:rows])
+        for r in range(rows):
+            env.M[r] = [rng.standard_normal((tnmc.bond_dim(big.chi, big.Lx, big.Ly, r, c), 2,
+                                             tnmc.bond_dim(big.chi, big.Lx, big.Ly, r, c + 1))) ** 2
+                        for c in range(big.Lx)]
+        mean_flops = sum(algorithmic_flops(i) for i in insts) / len(insts)
+        scale = algorithmic_flops(big) / mean_flops
+        return env, big, rows, ("random positive tensors with the bond dimensions of the first %d rows of a "
+                                "%dx%d chi=%d instance, rate scaled by %.3f to the batch's mean work per proposal"
+                                % (rows, big.Ly, big.Lx, big.chi, scale)), scale
     if inst.Lx * inst.Ly <= 4096:
         env = tnmc.build_env(inst.Jh, inst.Jv, inst.h, inst.beta, inst.chi)
-        return env, inst, inst.Ly, "oracle-built environment"
+        return env, inst, inst.Ly, "oracle-built environment", 1.0
     rows = min(inst.Ly, n_rows_cap)
     rng = np.random.default_rng(0)
     env = tnmc.Env(inst.Lx, rows, inst.beta, inst.chi, inst.Jh[:rows], inst.Jv[:rows - 1], inst.h[:rows])
@@ -357,7 +563,7 @@ def _oracle_workload(config, n_rows_cap):
         env.M[r] = [rng.standard_normal((tnmc.bond_dim(inst.chi, inst.Lx, inst.Ly, r, c), 2,
                                          tnmc.bond_dim(inst.chi, inst.Lx, inst.Ly, r, c + 1))) ** 2
                     for c in range(inst.Lx)]
-    return env, inst, rows, "random positive tensors with the bond dimensions of the first %d rows" % rows
+    return env, inst, rows, "random positive tensors with the bond dimensions of the first %d rows" % rows, 1.0
 
 
 def cpu_baseline(config, prec, seconds):
@@ -375,7 +581,7 @@ def cpu_baseline(config, prec, seconds):
 
 def _cpu_rate(config, seconds):
     from oracle import tnmc
-    env, inst, rows, how = _oracle_workload(config, 4)
+    env, inst, rows, how, wscale = _oracle_workload(config, 4)
     nB = 1
     t = 0.0
     while True:
@@ -385,7 +591,7 @@ def _cpu_rate(config, seconds):
         if t > seconds / 4 or nB >= (1 << 16):
             break
         nB *= 4
-    per_sample = t / nB * (inst.Ly / rows)
+    per_sample = t / nB * (inst.Ly / rows) / wscale
     return {"value": 1.0 / per_sample, "unit": "proposals/s", "cores": 1, "kind": "oracle",
             "sample": "%d proposals of %s over %d of %d rows (%s), scaled to the full lattice; numpy, 1 thread"
                       % (nB, config, rows, inst.Ly, how)}
@@ -403,7 +609,7 @@ def run_reference(args):
     if rank != 0:
         return
     from oracle import tnmc
-    env, inst, rows, how = _oracle_workload(args.config, 4)
+    env, inst, rows, how, wscale = _oracle_workload(args.config, 4)
     fac, Bdef, Cdef, pdef, desc = CONFIGS[args.config]
     real = rows == inst.Ly and how.startswith("oracle")
     nB = args.cpu_batch
@@ -429,7 +635,7 @@ def run_reference(args):
             a, cs, clq, cE = tnmc.mh_scan(inst.beta, C, T, sp, lq, E, cs, clq, cE, seed=1, step_offset=i * T)
             acc_n += int(a.sum())
         times.append(time.time() - t0)
-    scale = inst.Ly / rows
+    scale = inst.Ly / rows / wscale
     per_step = statistics.mean(times) * scale
     if real:
         value, unit = acc_n / (sum(times) * scale), "accepted samples/s"
@@ -467,6 +673,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.config == "c3":
+        run_batched(args)
     else:
         run_tnmc(args)
 

@@ -56,6 +56,7 @@ typedef enum { TNMC_F64 = 0, TNMC_F32 = 1, TNMC_BF16 = 2 } tnmc_precision;
 #define TNMC_FLAG_NUMERIC 1
 
 typedef struct tnmc_env tnmc_env;
+typedef struct tnmc_batch tnmc_batch;
 
 typedef struct {
   int Lx, Ly;
@@ -73,6 +74,22 @@ typedef struct {
   double logZ;            /* log Z~ of the truncated contraction                   */
   int64_t bytes;          /* device bytes held by the env                          */
 } tnmc_env_info_t;
+
+typedef struct {
+  int n;                   /* instances                                           */
+  int precision;           /* TNMC_F64 or TNMC_F32                                */
+  int tile;                /* samples per work item (64 or 128)                   */
+  int order;               /* 0 instance order, 1 longest instance first          */
+  int grid;                /* CTAs of the persistent launch                       */
+  int64_t chains;          /* chains per instance C                               */
+  int64_t proposal_rows;   /* sum_i B_i                                           */
+  int64_t proposal_bytes;  /* sum_i B_i Lx_i Ly_i (the proposal spin arena)       */
+  int64_t chain_rows;      /* n C                                                 */
+  int64_t chain_bytes;     /* sum_i C Lx_i Ly_i (the chain spin arena)            */
+  int64_t items;           /* work items of one proposal launch                   */
+  int64_t smem_bytes;      /* dynamic shared memory per CTA                       */
+  int64_t scratch_bytes;   /* device bytes of the per-CTA right-vector stacks     */
+} tnmc_batch_info_t;
 
 /* Thread-local text of the last error (empty string if none). */
 const char* tnmc_last_error(void);
@@ -218,6 +235,93 @@ tnmc_status tnmc_logq_backward(const tnmc_env* env, int64_t B, const int8_t* spi
  */
 tnmc_status tnmc_env_get_params(const tnmc_env* env, float* dst, void* stream);
 tnmc_status tnmc_env_set_params(tnmc_env* env, const float* src, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Batched persistent form: many independent instances (for instance disorder
+ * realisations of uneven L and chi) in single launches.  Each instance follows
+ * exactly the single-instance definitions above; batching changes only how the
+ * work is scheduled.
+ * ------------------------------------------------------------------------- */
+
+/*
+ * Build n instances' environments in ONE builder launch (one CTA per
+ * instance), then derive their sampler copies.  Arguments are arrays of n
+ * (lattices, betas, chis) with the meaning of tnmc_build_env; out[n] receives
+ * the envs (free each with tnmc_env_free).  On error nothing is returned and
+ * the message names the instance.
+ */
+tnmc_status tnmc_build_env_batched(int n, const tnmc_lattice* lats, const double* beta, const int* chi,
+                                   int precision_mask, void* stream, tnmc_env** out);
+
+/*
+ * A plan over n built envs (which must outlive it): B[i] proposals per step
+ * for instance i (a multiple of `chains`), `chains` Markov chains per instance
+ * (chain c of instance i consumes proposals c*T_i .. c*T_i+T_i-1 of that
+ * instance, T_i = B[i] / chains), sampler arithmetic `precision` (TNMC_F64 or
+ * TNMC_F32; every env must hold that copy), `tile` samples per work item (64
+ * or 128) and the item `order` (0: instance order; 1: instances with the
+ * largest per-sample cost first).  Work items are (instance, tile) pairs taken
+ * by a persistent grid from an atomic counter.  Allocates the plan's device
+ * tables and per-CTA scratch; synchronises `stream` before returning.
+ * Proposal arrays are concatenated by instance: instance i's proposals are rows
+ * prop_row[i] .. prop_row[i]+B[i]-1 of logq / energy / flags and bytes
+ * prop_spin[i] .. of the spin arena (layout [B_i][Ly_i][Lx_i]); chains
+ * likewise (see tnmc_batch_layout).  A plan serves one stream at a time.
+ */
+tnmc_status tnmc_batch_create(int n, tnmc_env* const* envs, const int64_t* B, int64_t chains, int precision,
+                              int tile, int order, void* stream, tnmc_batch** out);
+tnmc_status tnmc_batch_free(tnmc_batch* plan);
+tnmc_status tnmc_batch_info(const tnmc_batch* plan, tnmc_batch_info_t* info);
+
+/* Host arrays [n] (any may be NULL): first proposal row, proposal spin byte
+ * offset, first chain row (= i * chains), chain spin byte offset per instance. */
+tnmc_status tnmc_batch_layout(const tnmc_batch* plan, int64_t* prop_row, int64_t* prop_spin,
+                              int64_t* chain_row, int64_t* chain_spin);
+
+/*
+ * The plan's device-resident (seed, step k).  At step k instance i draws the
+ * samples (i << 40) + k B_i + b, b < B_i (so its proposals equal tnmc_sample
+ * with sample_offset (i << 40) + k B_i), and its MH scan uses step offsets
+ * (i << 40) + k T_i (tnmc_mh_step's step_offset).  set writes both values;
+ * advance adds 1 to k on the device, so a captured CUDA graph of
+ * sample + mh + advance replays successive steps.
+ */
+tnmc_status tnmc_batch_set_step(tnmc_batch* plan, uint64_t seed, uint64_t step, void* stream);
+tnmc_status tnmc_batch_advance(tnmc_batch* plan, void* stream);
+
+/*
+ * One persistent launch drawing every instance's B_i proposals (spins, exact
+ * log q, exact energy, flags as tnmc_sample).  Issues no allocation and no
+ * synchronisation, so it may be captured in a CUDA graph.
+ * prop_spins  device int8, proposal_bytes (output); prop_logq / prop_energy
+ * device double [proposal_rows]; flags device int32 [proposal_rows] or NULL.
+ */
+tnmc_status tnmc_sample_batched(tnmc_batch* plan, int8_t* prop_spins, double* prop_logq, double* prop_energy,
+                                int32_t* flags, void* stream);
+
+/* Forced evaluation (tnmc_logq) of a whole proposal arena in one persistent launch. */
+tnmc_status tnmc_logq_batched(tnmc_batch* plan, const int8_t* prop_spins, double* prop_logq,
+                              double* prop_energy, int32_t* flags, void* stream);
+
+/*
+ * Random +-1 start of every chain (Algorithm 1, second step): chain c of
+ * instance i takes the random-start stream with chain id (i << 32) | c, then its
+ * forced log q and energy.  chain_spins device int8 [chain_bytes];
+ * chain_logq / chain_energy device double [chain_rows].
+ */
+tnmc_status tnmc_batch_init_chains(tnmc_batch* plan, uint64_t seed, int8_t* chain_spins, double* chain_logq,
+                                   double* chain_energy, void* stream);
+
+/*
+ * The MH scan (eq. mh-acc, Algorithm 1) of every chain of every instance in
+ * one launch, with the plan's (seed, step); per instance identical to
+ * tnmc_mh_step(env_i, chains, T_i, ..., seed, (i << 40) + k T_i, ...).
+ * accepted  device uint8 [proposal_rows] or NULL
+ * n_accepted  device int64 [n] or NULL; instance i's count is ADDED to entry i
+ */
+tnmc_status tnmc_mh_batched(tnmc_batch* plan, const int8_t* prop_spins, const double* prop_logq,
+                            const double* prop_energy, int8_t* chain_spins, double* chain_logq,
+                            double* chain_energy, uint8_t* accepted, int64_t* n_accepted, void* stream);
 
 #ifdef __cplusplus
 }

@@ -1,0 +1,139 @@
+"""Batched persistent form: tile autotuner and CUDA-graph step runner.
+
+Many independent instances (disorder realisations of uneven L and chi) are
+sampled by one persistent launch of the library (``tnmc_sample_batched``) and
+scanned by one batched MH launch (``tnmc_mh_batched``).  This module picks the
+launch shape and captures the per-step launches in a CUDA graph:
+
+* ``autotune`` times every candidate (tile of 64 or 128 samples per work item x
+  item order "instance" or "cost"-descending) on the actual workload with CUDA
+  events and caches the fastest in a JSON file keyed by the workload and the
+  device;
+* ``BatchRunner`` owns the plan, the proposal and chain buffers, and replays a
+  captured graph of sample -> MH -> advance, so a step costs one graph launch.
+
+The arithmetic is the library's; nothing here computes.
+"""
+import hashlib
+import json
+import os
+
+from . import binding
+
+CACHE_PATH = os.path.join(binding.HERE, "_build", "batch_tiles.json")
+CANDIDATES = [(tile, order) for tile in (64, 128) for order in ("instance", "cost")]
+
+
+def workload_key(envs, B, chains, precision):
+    import torch
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    sig = {
+        "device": props.name, "sms": props.multi_processor_count, "precision": precision, "chains": int(chains),
+        "inst": [[e.Lx, e.Ly, e.chi, int(b)] for e, b in zip(envs, B)],
+    }
+    return hashlib.sha1(json.dumps(sig, sort_keys=True).encode()).hexdigest()
+
+
+def _load(path):
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def time_plan(plan, reps=3, warmup=1, seed=0):
+    """Mean milliseconds of one tnmc_sample_batched launch of `plan`."""
+    import torch
+    out = plan.alloc_proposals()
+    plan.set_step(seed, 0)
+    for _ in range(warmup):
+        plan.sample(out)
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(reps):
+        plan.sample(out)
+    t1.record()
+    torch.cuda.synchronize()
+    return t0.elapsed_time(t1) / reps
+
+
+def autotune(envs, B, chains=1, precision="f32", cache_path=CACHE_PATH, reps=3, refresh=False, log=None):
+    """Fastest (tile, order) for this workload; times every candidate once, then caches it."""
+    import numpy as np
+    B = [int(b) for b in np.broadcast_to(np.asarray(B), (len(envs),))]
+    key = workload_key(envs, B, chains, precision)
+    cache = _load(cache_path)
+    if not refresh and key in cache:
+        return cache[key]
+    results = []
+    for tile, order in CANDIDATES:
+        plan = binding.Batch(envs, B, chains=chains, precision=precision, tile=tile, order=order)
+        ms = time_plan(plan, reps=reps)
+        plan.free()
+        results.append({"tile": tile, "order": order, "ms": ms})
+        if log:
+            log("autotune tile=%d order=%s: %.3f ms" % (tile, order, ms))
+    best = min(results, key=lambda r: r["ms"])
+    best = dict(best, candidates=results)
+    cache[key] = best
+    os.makedirs(os.path.dirname(cache_path), exist_ok=True)
+    tmp = cache_path + ".tmp%d" % os.getpid()
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1)
+    os.replace(tmp, cache_path)
+    return best
+
+
+class BatchRunner:
+    """Plan + buffers + captured graph of one MH step over every instance.
+
+    step k: proposals of every instance (tnmc_sample_batched), the MH scan of
+    every chain (tnmc_mh_batched), then k += 1 on the device.
+    """
+
+    def __init__(self, envs, B, chains=1, precision="f32", tile=None, order=None, seed=0, tune=True,
+                 cache_path=CACHE_PATH, log=None):
+        import torch
+        if tile is None or order is None:
+            if tune:
+                best = autotune(envs, B, chains, precision, cache_path=cache_path, log=log)
+                tile, order = best["tile"], best["order"]
+            else:
+                tile, order = 128, "cost"
+        self.plan = binding.Batch(envs, B, chains=chains, precision=precision, tile=tile, order=order)
+        self.seed = seed
+        self.prop = self.plan.alloc_proposals()
+        self.chain = self.plan.init_chains(seed)
+        inf = self.plan.info()
+        self.accepted = torch.zeros(inf["proposal_rows"], dtype=torch.uint8, device="cuda")
+        self.n_accepted = torch.zeros(self.plan.n, dtype=torch.int64, device="cuda")
+        self.plan.set_step(seed, 0)
+        self.graph = None
+
+    def _launch(self):
+        self.plan.sample(self.prop)
+        self.plan.mh(self.prop, self.chain, self.accepted, self.n_accepted)
+        self.plan.advance()
+
+    def step_eager(self):
+        self._launch()
+
+    def capture(self):
+        """Capture one step in a CUDA graph (the launches allocate nothing)."""
+        import torch
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            self._launch()
+        torch.cuda.synchronize()
+        self.graph = g
+        return g
+
+    def step(self):
+        if self.graph is None:
+            self.capture()
+        self.graph.replay()

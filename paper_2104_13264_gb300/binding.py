@@ -35,6 +35,13 @@ class _Info(ctypes.Structure):
                 ("beta", ctypes.c_double), ("logZ", ctypes.c_double), ("bytes", ctypes.c_int64)]
 
 
+class _BatchInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("precision", ctypes.c_int), ("tile", ctypes.c_int), ("order", ctypes.c_int),
+                ("grid", ctypes.c_int), ("chains", ctypes.c_int64), ("proposal_rows", ctypes.c_int64),
+                ("proposal_bytes", ctypes.c_int64), ("chain_rows", ctypes.c_int64), ("chain_bytes", ctypes.c_int64),
+                ("items", ctypes.c_int64), ("smem_bytes", ctypes.c_int64), ("scratch_bytes", ctypes.c_int64)]
+
+
 _P = ctypes.c_void_p
 _I64 = ctypes.c_int64
 _U64 = ctypes.c_uint64
@@ -55,6 +62,17 @@ SIGNATURES = {
     "tnmc_logq_backward": ([_P, _I64, _P, _P, _P, _P], _INT),
     "tnmc_env_get_params": ([_P, _P, _P], _INT),
     "tnmc_env_set_params": ([_P, _P, _P], _INT),
+    "tnmc_build_env_batched": ([_INT, _P, _P, _P, _INT, _P, _P], _INT),
+    "tnmc_batch_create": ([_INT, _P, _P, _I64, _INT, _INT, _INT, _P, ctypes.POINTER(_P)], _INT),
+    "tnmc_batch_free": ([_P], _INT),
+    "tnmc_batch_info": ([_P, ctypes.POINTER(_BatchInfo)], _INT),
+    "tnmc_batch_layout": ([_P, _P, _P, _P, _P], _INT),
+    "tnmc_batch_set_step": ([_P, _U64, _U64, _P], _INT),
+    "tnmc_batch_advance": ([_P, _P], _INT),
+    "tnmc_sample_batched": ([_P, _P, _P, _P, _P, _P], _INT),
+    "tnmc_logq_batched": ([_P, _P, _P, _P, _P, _P], _INT),
+    "tnmc_batch_init_chains": ([_P, _U64, _P, _P, _P, _P], _INT),
+    "tnmc_mh_batched": ([_P, _P, _P, _P, _P, _P, _P, _P, _P, _P], _INT),
 }
 
 
@@ -107,6 +125,13 @@ class Env:
         self._h = None
         _check(lib().tnmc_build_env(ctypes.byref(lat), self.beta, self.chi, mask, _stream(stream), ctypes.byref(out)))
         self._h = out
+
+    @classmethod
+    def _wrap(cls, handle, Lx, Ly, beta, chi):
+        self = cls.__new__(cls)
+        self.Lx, self.Ly, self.beta, self.chi = Lx, Ly, float(beta), int(chi)
+        self._h = handle
+        return self
 
     @classmethod
     def from_instance(cls, inst, precisions=("f64",), chi=None, stream=None):
@@ -229,3 +254,141 @@ def logq_backward(env, spins, weights, stream=None):
     grad = torch.empty(param_count(env), dtype=torch.float32, device="cuda")
     _check(lib().tnmc_logq_backward(env.handle, spins.shape[0], _ptr(spins), _ptr(w), _ptr(grad), _stream(stream)))
     return grad
+
+
+def _lattice_arrays(inst):
+    h = np.ascontiguousarray(inst.h, dtype=np.float64)
+    Ly, Lx = h.shape
+    Jh = np.ascontiguousarray(np.asarray(inst.Jh, dtype=np.float64).reshape(Ly, max(Lx - 1, 0)))
+    Jv = np.ascontiguousarray(np.asarray(inst.Jv, dtype=np.float64).reshape(max(Ly - 1, 0), Lx))
+    return Jh, Jv, h
+
+
+def build_envs_batched(insts, precisions=("f64",), stream=None):
+    """Build every instance's environment in one builder launch; returns a list of Env."""
+    n = len(insts)
+    arrays = [_lattice_arrays(i) for i in insts]
+    lats = (_Lattice * n)()
+    for k, (Jh, Jv, h) in enumerate(arrays):
+        Ly, Lx = h.shape
+        lats[k] = _Lattice(Lx, Ly, Jh.ctypes.data if Jh.size else None, Jv.ctypes.data if Jv.size else None,
+                           h.ctypes.data)
+    beta = np.array([i.beta for i in insts], dtype=np.float64)
+    chi = np.array([i.chi for i in insts], dtype=np.int32)
+    mask = 0
+    for p in precisions:
+        mask |= 1 << PRECISIONS[p]
+    out = (_P * n)()
+    _check(lib().tnmc_build_env_batched(n, ctypes.cast(lats, _P), beta.ctypes.data, chi.ctypes.data, mask,
+                                        _stream(stream), ctypes.cast(out, _P)))
+    return [Env._wrap(_P(out[k]), arrays[k][2].shape[1], arrays[k][2].shape[0], insts[k].beta, insts[k].chi)
+            for k in range(n)]
+
+
+class Batch:
+    """A plan over many envs: one persistent launch samples them all (see tnmc_batch_create).
+
+    Keeps references to the envs, which must outlive the plan.
+    """
+
+    ORDERS = {"instance": 0, "cost": 1}
+
+    def __init__(self, envs, B, chains=1, precision="f32", tile=128, order="cost", stream=None):
+        n = len(envs)
+        self.envs = list(envs)
+        self.B = np.ascontiguousarray(np.broadcast_to(np.asarray(B, dtype=np.int64), (n,)))
+        handles = (_P * n)(*[e.handle.value for e in self.envs])
+        out = _P()
+        self._h = None
+        _check(lib().tnmc_batch_create(n, ctypes.cast(handles, _P), self.B.ctypes.data, int(chains),
+                                       PRECISIONS[precision], int(tile), self.ORDERS[order], _stream(stream),
+                                       ctypes.byref(out)))
+        self._h = out
+        self.n, self.chains, self.precision, self.tile, self.order = n, int(chains), precision, int(tile), order
+        self.prop_row = np.zeros(n, dtype=np.int64)
+        self.prop_spin = np.zeros(n, dtype=np.int64)
+        self.chain_row = np.zeros(n, dtype=np.int64)
+        self.chain_spin = np.zeros(n, dtype=np.int64)
+        _check(lib().tnmc_batch_layout(self._h, self.prop_row.ctypes.data, self.prop_spin.ctypes.data,
+                                       self.chain_row.ctypes.data, self.chain_spin.ctypes.data))
+
+    def info(self):
+        i = _BatchInfo()
+        _check(lib().tnmc_batch_info(self._h, ctypes.byref(i)))
+        return {k: getattr(i, k) for k, _ in _BatchInfo._fields_}
+
+    def alloc_proposals(self):
+        """(spins arena int8, logq, energy, flags) cuda tensors for one step."""
+        import torch
+        inf = self.info()
+        dev = torch.device("cuda")
+        return (torch.empty(inf["proposal_bytes"], dtype=torch.int8, device=dev),
+                torch.empty(inf["proposal_rows"], dtype=torch.float64, device=dev),
+                torch.empty(inf["proposal_rows"], dtype=torch.float64, device=dev),
+                torch.empty(inf["proposal_rows"], dtype=torch.int32, device=dev))
+
+    def alloc_chains(self):
+        import torch
+        inf = self.info()
+        dev = torch.device("cuda")
+        return (torch.empty(inf["chain_bytes"], dtype=torch.int8, device=dev),
+                torch.empty(inf["chain_rows"], dtype=torch.float64, device=dev),
+                torch.empty(inf["chain_rows"], dtype=torch.float64, device=dev))
+
+    def view(self, arena, i, chains=False):
+        """Instance i's [rows, Ly, Lx] view of a spin arena."""
+        e = self.envs[i]
+        off = int(self.chain_spin[i] if chains else self.prop_spin[i])
+        rows = self.chains if chains else int(self.B[i])
+        return arena[off:off + rows * e.Lx * e.Ly].view(rows, e.Ly, e.Lx)
+
+    def rows(self, arr, i, chains=False):
+        off = int(self.chain_row[i] if chains else self.prop_row[i])
+        rows = self.chains if chains else int(self.B[i])
+        return arr[off:off + rows]
+
+    def set_step(self, seed, step, stream=None):
+        _check(lib().tnmc_batch_set_step(self._h, seed, step, _stream(stream)))
+
+    def advance(self, stream=None):
+        _check(lib().tnmc_batch_advance(self._h, _stream(stream)))
+
+    def sample(self, out, stream=None):
+        sp, lq, E, fl = out
+        _check(lib().tnmc_sample_batched(self._h, _ptr(sp), _ptr(lq), _ptr(E), _ptr(fl), _stream(stream)))
+        return out
+
+    def logq(self, spins, out=None, stream=None):
+        import torch
+        inf = self.info()
+        if out is None:
+            out = (torch.empty(inf["proposal_rows"], dtype=torch.float64, device=spins.device),
+                   torch.empty(inf["proposal_rows"], dtype=torch.float64, device=spins.device),
+                   torch.empty(inf["proposal_rows"], dtype=torch.int32, device=spins.device))
+        lq, E, fl = out
+        _check(lib().tnmc_logq_batched(self._h, _ptr(spins), _ptr(lq), _ptr(E), _ptr(fl), _stream(stream)))
+        return out
+
+    def init_chains(self, seed, out=None, stream=None):
+        out = self.alloc_chains() if out is None else out
+        sp, lq, E = out
+        _check(lib().tnmc_batch_init_chains(self._h, seed, _ptr(sp), _ptr(lq), _ptr(E), _stream(stream)))
+        return out
+
+    def mh(self, prop, chain, accepted=None, n_accepted=None, stream=None):
+        ps, plq, pE = prop[:3]
+        cs, clq, cE = chain
+        _check(lib().tnmc_mh_batched(self._h, _ptr(ps), _ptr(plq), _ptr(pE), _ptr(cs), _ptr(clq), _ptr(cE),
+                                     _ptr(accepted), _ptr(n_accepted), _stream(stream)))
+        return accepted
+
+    def free(self):
+        if self._h is not None and self._h.value:
+            lib().tnmc_batch_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

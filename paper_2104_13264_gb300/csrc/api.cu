@@ -40,16 +40,15 @@ bool is_integer_array(const double* p, size_t n) {
 
 }  // namespace
 
-extern "C" {
+namespace {
 
-const char* tnmc_last_error(void) { return g_err; }
-
-tnmc_status tnmc_build_env(const tnmc_lattice* lat, double beta, int chi, int precision_mask, void* stream,
-                           tnmc_env** out) {
+// Checks the arguments, allocates the environment's arena and uploads the
+// couplings; the tensors are written by a later builder launch.
+tnmc_status env_create(const tnmc_lattice* lat, double beta, int chi, int precision_mask, cudaStream_t s,
+                       tnmc_env** out) {
   using namespace tnmc;
-  g_err[0] = 0;
-  CHECK_ARG(lat && out, "lat and out must be non-null");
   *out = nullptr;
+  CHECK_ARG(lat, "lattice must be non-null");
   const int Lx = lat->Lx, Ly = lat->Ly;
   CHECK_ARG(Lx >= 1 && Ly >= 1 && Lx <= 4096 && Ly <= 4096, "lattice %d x %d out of range", Ly, Lx);
   CHECK_ARG(chi >= 1 && chi <= kMaxChi, "chi = %d must be in [1, %d]", chi, kMaxChi);
@@ -93,7 +92,6 @@ tnmc_status tnmc_build_env(const tnmc_lattice* lat, double beta, int chi, int pr
   const size_t odisc = take((size_t)Ly * (Lx + 1) * 8), ologZ = take(8), ostat = take(8);
   const size_t total = off;
 
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
   tnmc_env* env = new (std::nothrow) tnmc_env();
   if (!env) {
     tnmc_set_error("host allocation failed");
@@ -147,8 +145,6 @@ tnmc_status tnmc_build_env(const tnmc_lattice* lat, double beta, int chi, int pr
   env->Jv32 = reinterpret_cast<float*>(base + oJv32);
 
   tnmc_status st = TNMC_OK;
-  void* work = nullptr;
-  const size_t wbytes = tnmc_build_work_bytes(Lx, Ly, P);
   do {
     if (cudaMemsetAsync(base, 0, total, s) != cudaSuccess) { st = TNMC_E_CUDA; break; }
     if (nJh && cudaMemcpyAsync(const_cast<double*>(d.Jh), lat->Jh, nJh * 8, cudaMemcpyHostToDevice, s) != cudaSuccess) { st = TNMC_E_CUDA; break; }
@@ -156,7 +152,55 @@ tnmc_status tnmc_build_env(const tnmc_lattice* lat, double beta, int chi, int pr
     if (cudaMemcpyAsync(const_cast<double*>(d.h), lat->h, nh * 8, cudaMemcpyHostToDevice, s) != cudaSuccess) { st = TNMC_E_CUDA; break; }
     // the host arrays may be released as soon as this call returns
     if (cudaStreamSynchronize(s) != cudaSuccess) { st = TNMC_E_CUDA; break; }
+  } while (0);
+  if (st != TNMC_OK) {
+    if (!g_err[0]) tnmc_set_error("CUDA error while uploading the couplings: %s", cudaGetErrorString(cudaGetLastError()));
+    (void)cudaStreamSynchronize(s);
+    cudaFree(base);
+    delete env;
+    return st;
+  }
+  *out = env;
+  return TNMC_OK;
+}
+
+void env_destroy(tnmc_env* env, cudaStream_t s) {
+  if (!env) return;
+  (void)cudaStreamSynchronize(s);
+  if (env->scratch.ptr) cudaFree(env->scratch.ptr);
+  cudaFree(env->arena);
+  delete env;
+}
+
+// The sampler copies of a built environment.
+tnmc_status env_derive(tnmc_env* env, cudaStream_t s) {
+  tnmc_status st = tnmc_launch_derive(env, env->precision_mask, s);
+  if (st == TNMC_OK && (env->precision_mask & (1 << TNMC_BF16))) st = tnmc_launch_derive_tc(env, s);
+  return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* tnmc_last_error(void) { return g_err; }
+
+tnmc_status tnmc_build_env(const tnmc_lattice* lat, double beta, int chi, int precision_mask, void* stream,
+                           tnmc_env** out) {
+  using namespace tnmc;
+  g_err[0] = 0;
+  CHECK_ARG(lat && out, "lat and out must be non-null");
+  *out = nullptr;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  tnmc_env* env = nullptr;
+  tnmc_status st = env_create(lat, beta, chi, precision_mask, s, &env);
+  if (st != TNMC_OK) return st;
+  const DeviceEnv& d = env->d;
+  void* work = nullptr;
+  const size_t wbytes = tnmc_build_work_bytes(d.Lx, d.Ly, d.P);
+  do {
     if (cudaMallocAsync(&work, wbytes, s) != cudaSuccess) {
+      (void)cudaGetLastError();
       work = nullptr;
       st = TNMC_E_NOMEM;
       tnmc_set_error("cannot allocate %zu bytes of builder scratch", wbytes);
@@ -164,19 +208,66 @@ tnmc_status tnmc_build_env(const tnmc_lattice* lat, double beta, int chi, int pr
     }
     st = tnmc_launch_build(env, s, work, wbytes);
     if (st != TNMC_OK) break;
-    st = tnmc_launch_derive(env, mask, s);
-    if (st != TNMC_OK) break;
-    if (mask & (1 << TNMC_BF16)) st = tnmc_launch_derive_tc(env, s);
+    st = env_derive(env, s);
   } while (0);
   if (work) (void)cudaFreeAsync(work, s);
   if (st != TNMC_OK) {
     if (st == TNMC_E_CUDA && !g_err[0]) tnmc_set_error("CUDA error while building: %s", cudaGetErrorString(cudaGetLastError()));
-    (void)cudaStreamSynchronize(s);
-    cudaFree(base);
-    delete env;
+    env_destroy(env, s);
     return st;
   }
   *out = env;
+  return TNMC_OK;
+}
+
+tnmc_status tnmc_build_env_batched(int n, const tnmc_lattice* lats, const double* beta, const int* chi,
+                                   int precision_mask, void* stream, tnmc_env** out) {
+  using namespace tnmc;
+  g_err[0] = 0;
+  CHECK_ARG(n >= 0, "n = %d must be >= 0", n);
+  CHECK_ARG(n == 0 || (lats && beta && chi && out), "lats, beta, chi and out must be non-null");
+  if (n == 0) return TNMC_OK;
+  for (int i = 0; i < n; ++i) out[i] = nullptr;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::vector<tnmc_env*> envs(n, nullptr);
+  std::vector<size_t> woff(n);
+  tnmc_status st = TNMC_OK;
+  size_t wtotal = 0;
+  for (int i = 0; i < n && st == TNMC_OK; ++i) {
+    st = env_create(&lats[i], beta[i], chi[i], precision_mask, s, &envs[i]);
+    if (st != TNMC_OK) {
+      char msg[512];
+      snprintf(msg, sizeof msg, "instance %d: %s", i, g_err);
+      tnmc_set_error("%s", msg);
+      break;
+    }
+    const DeviceEnv& d = envs[i]->d;
+    woff[i] = wtotal;
+    wtotal += align256(tnmc_build_work_bytes(d.Lx, d.Ly, d.P));
+  }
+  void* work = nullptr;
+  void* args = nullptr;
+  if (st == TNMC_OK) {
+    do {
+      if (cudaMallocAsync(&work, wtotal, s) != cudaSuccess ||
+          cudaMallocAsync(&args, (size_t)n * tnmc_build_args_bytes(), s) != cudaSuccess) {
+        (void)cudaGetLastError();
+        st = TNMC_E_NOMEM;
+        tnmc_set_error("cannot allocate %zu bytes of builder scratch", wtotal);
+        break;
+      }
+      st = tnmc_launch_build_batched(envs.data(), n, work, woff.data(), args, s);
+      for (int i = 0; i < n && st == TNMC_OK; ++i) st = env_derive(envs[i], s);
+    } while (0);
+  }
+  if (work) (void)cudaFreeAsync(work, s);
+  if (args) (void)cudaFreeAsync(args, s);
+  if (st != TNMC_OK) {
+    if (st == TNMC_E_CUDA && !g_err[0]) tnmc_set_error("CUDA error while building: %s", cudaGetErrorString(cudaGetLastError()));
+    for (int i = 0; i < n; ++i) env_destroy(envs[i], s);
+    return st;
+  }
+  for (int i = 0; i < n; ++i) out[i] = envs[i];
   return TNMC_OK;
 }
 

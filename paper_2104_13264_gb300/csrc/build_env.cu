@@ -19,6 +19,8 @@
 // of one site runs in shared memory.  All arithmetic is FP64.
 #include <math.h>
 
+#include <new>
+
 #include "common.cuh"
 
 namespace tnmc {
@@ -42,6 +44,7 @@ struct BuildArgs {
   double* work;   // (Lx + 2) slots of 8 P^2 doubles
   int32_t* status;
   int32_t* esz;   // [Ly][Lx+1] even-sector size of every bond (Z2 builder)
+  int z2;         // parity-sector builder (all fields zero)
 };
 
 
@@ -503,8 +506,7 @@ __device__ double svd_sweep(const BuildArgs& a, Shared& sh, int r) {
   return logs;
 }
 
-__global__ void __launch_bounds__(kBuildThreads) build_env_kernel(BuildArgs a) {
-  extern __shared__ double smem[];
+__device__ void build_env_body(const BuildArgs& a, double* smem) {
   const int Lx = a.Lx, P = a.P;
   Shared sh;
   sh.W = smem;
@@ -906,8 +908,7 @@ __device__ double svd_sweep_z2(const BuildArgs& a, ShZ2& sh, int r) {
   return logs;
 }
 
-__global__ void __launch_bounds__(kBuildThreads) build_env_z2_kernel(BuildArgs a) {
-  extern __shared__ double smem[];
+__device__ void build_env_z2_body(const BuildArgs& a, double* smem) {
   const int Lx = a.Lx, P = a.P;
   ShZ2 sh;
   sh.W = smem;
@@ -995,6 +996,22 @@ __global__ void __launch_bounds__(kBuildThreads) build_env_z2_kernel(BuildArgs a
   }
 }
 
+__global__ void __launch_bounds__(kBuildThreads) build_env_kernel(BuildArgs a) {
+  extern __shared__ double smem[];
+  build_env_body(a, smem);
+}
+__global__ void __launch_bounds__(kBuildThreads) build_env_z2_kernel(BuildArgs a) {
+  extern __shared__ double smem[];
+  build_env_z2_body(a, smem);
+}
+// Many instances in one launch, one CTA each (independent problems).
+__global__ void __launch_bounds__(kBuildThreads) build_env_batched_kernel(const BuildArgs* list) {
+  extern __shared__ double smem[];
+  const BuildArgs a = list[blockIdx.x];
+  if (a.z2) build_env_z2_body(a, smem);
+  else build_env_body(a, smem);
+}
+
 }  // namespace
 }  // namespace tnmc
 
@@ -1007,13 +1024,9 @@ static size_t build_smem_bytes(int Lx, int P) {
   return (size_t)(6 * P * P + 4 * P + 64) * sizeof(double) + (size_t)(3 * Lx + 4 + 4 * P + 8) * sizeof(int);
 }
 
-tnmc_status tnmc_launch_build(tnmc_env* env, cudaStream_t stream, void* work, size_t work_bytes) {
+static tnmc::BuildArgs make_build_args(tnmc_env* env, void* work) {
   using namespace tnmc;
   const DeviceEnv& d = env->d;
-  if (work_bytes < tnmc_build_work_bytes(d.Lx, d.Ly, d.P)) {
-    tnmc_set_error("build scratch too small");
-    return TNMC_E_INVALID_ARG;
-  }
   BuildArgs a;
   a.Lx = d.Lx;
   a.Ly = d.Ly;
@@ -1032,6 +1045,18 @@ tnmc_status tnmc_launch_build(tnmc_env* env, cudaStream_t stream, void* work, si
   a.work = static_cast<double*>(work);
   a.status = d.status;
   a.esz = env->esz;
+  a.z2 = d.z2;
+  return a;
+}
+
+tnmc_status tnmc_launch_build(tnmc_env* env, cudaStream_t stream, void* work, size_t work_bytes) {
+  using namespace tnmc;
+  const DeviceEnv& d = env->d;
+  if (work_bytes < tnmc_build_work_bytes(d.Lx, d.Ly, d.P)) {
+    tnmc_set_error("build scratch too small");
+    return TNMC_E_INVALID_ARG;
+  }
+  BuildArgs a = make_build_args(env, work);
   const size_t smem = build_smem_bytes(d.Lx, d.P);
   int dev = 0, max_optin = 0;
   TNMC_CUDA_TRY(cudaGetDevice(&dev));
@@ -1050,3 +1075,41 @@ tnmc_status tnmc_launch_build(tnmc_env* env, cudaStream_t stream, void* work, si
   TNMC_CUDA_TRY(cudaGetLastError());
   return TNMC_OK;
 }
+
+tnmc_status tnmc_launch_build_batched(tnmc_env* const* envs, int n, void* work, const size_t* work_offsets,
+                                      void* args_dev, cudaStream_t stream) {
+  using namespace tnmc;
+  if (n <= 0) return TNMC_OK;
+  BuildArgs* host = new (std::nothrow) BuildArgs[n];
+  if (!host) {
+    tnmc_set_error("host allocation failed");
+    return TNMC_E_NOMEM;
+  }
+  size_t smem = 0;
+  for (int i = 0; i < n; ++i) {
+    host[i] = make_build_args(envs[i], static_cast<char*>(work) + work_offsets[i]);
+    const size_t si = build_smem_bytes(envs[i]->d.Lx, envs[i]->d.P);
+    if (si > smem) smem = si;
+  }
+  int dev = 0, max_optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e == cudaSuccess && smem > (size_t)max_optin) {
+    delete[] host;
+    tnmc_set_error("builder needs %zu bytes of shared memory (device allows %d)", smem, max_optin);
+    return TNMC_E_UNSUPPORTED;
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(args_dev, host, sizeof(BuildArgs) * n, cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);   // `host` is released below
+  delete[] host;
+  if (e != cudaSuccess) {
+    tnmc_set_error("batched build setup failed: %s", cudaGetErrorString(e));
+    return TNMC_E_CUDA;
+  }
+  TNMC_CUDA_TRY(cudaFuncSetAttribute(build_env_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  build_env_batched_kernel<<<n, kBuildThreads, smem, stream>>>(static_cast<const BuildArgs*>(args_dev));
+  TNMC_CUDA_TRY(cudaGetLastError());
+  return TNMC_OK;
+}
+
+size_t tnmc_build_args_bytes() { return sizeof(tnmc::BuildArgs); }

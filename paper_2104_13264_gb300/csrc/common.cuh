@@ -156,6 +156,9 @@ void tnmc_set_error(const char* fmt, ...);
 
 // launchers implemented in the kernel translation units
 tnmc_status tnmc_launch_build(tnmc_env* env, cudaStream_t stream, void* work, size_t work_bytes);
+tnmc_status tnmc_launch_build_batched(tnmc_env* const* envs, int n, void* work, const size_t* work_offsets,
+                                      void* args_dev, cudaStream_t stream);
+size_t tnmc_build_args_bytes();
 size_t tnmc_build_work_bytes(int Lx, int Ly, int P);
 tnmc_status tnmc_launch_derive(tnmc_env* env, int precision_mask, cudaStream_t stream);
 tnmc_status tnmc_launch_sample(const tnmc_env* env, int precision, int64_t B, uint64_t seed,

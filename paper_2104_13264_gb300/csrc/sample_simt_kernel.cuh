@@ -79,22 +79,21 @@ struct LogAcc<float> {
   __device__ double value() const { return lq; }
 };
 
+// One tile of NT samples of one instance.  Shared memory: VA, VB, VC [P][NT] and the
+// two bit rows [W][NT] carved from `smem` for this instance's P and W; `stack` is the
+// calling CTA's right-vector stack [Lx+1][P][NT].
 template <typename T, int NT>
-__global__ void __launch_bounds__(NT) sample_simt_kernel(SampleArgs<T> a) {
-  extern __shared__ unsigned char smem_raw[];
+__device__ void sample_simt_tile(const SampleArgs<T>& a, int64_t tile, unsigned char* smem, T* stack) {
   const int Lx = a.e.Lx, Ly = a.e.Ly, P = a.e.P;
   const int W = (Lx + 31) >> 5;
-  T* VA = reinterpret_cast<T*>(smem_raw);          // [P][NT]   Lambda / R ping
+  T* VA = reinterpret_cast<T*>(smem);               // [P][NT]   Lambda / R ping
   T* VB = VA + (size_t)P * NT;                       // [P][NT]   R pong / U[-1]
   T* VC = VB + (size_t)P * NT;                       // [P][NT]   U[+1]
   uint32_t* bits_prev = reinterpret_cast<uint32_t*>(VC + (size_t)P * NT);   // [W][NT]
   uint32_t* bits_cur = bits_prev + (size_t)W * NT;                            // [W][NT]
   const int tid = threadIdx.x;
-  const int64_t ntiles = (a.B + NT - 1) / NT;
-  T* stack = a.scratch + (size_t)blockIdx.x * (Lx + 1) * P * NT;
   const int n = Lx * Ly;
-
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  {
     const int64_t b = tile * NT + tid;
     const bool active = b < a.B;
     const uint64_t sample = a.offset + (uint64_t)b;
@@ -261,6 +260,14 @@ __global__ void __launch_bounds__(NT) sample_simt_kernel(SampleArgs<T> a) {
       if (flag) set_status(a.e.status, TNMC_E_NUMERIC);
     }
   }
+}
+
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) sample_simt_kernel(SampleArgs<T> a) {
+  extern __shared__ unsigned char smem_raw[];
+  const int64_t ntiles = (a.B + NT - 1) / NT;
+  T* stack = a.scratch + (size_t)blockIdx.x * (a.e.Lx + 1) * a.e.P * NT;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) sample_simt_tile<T, NT>(a, tile, smem_raw, stack);
 }
 
 }  // namespace
