@@ -4,8 +4,16 @@ The MH step keeps the chain exact whatever q is; making q larger on the states
 the chain actually visits raises the acceptance.  Each tuning step
   1. re-evaluates the chains' cached log q with the current q (it changed),
   2. draws proposals (FP32 sampler) and runs the MH scan,
-  3. takes the accepted proposals as the batch, loss = -mean log q over them,
-  4. backpropagates through tnmc_logq_backward and updates the FP32 tensors.
+  3. takes the states the chains occupied during the scan as the batch, each with
+     its residence time (the number of proposals it stayed for: an accepted
+     proposal until the next acceptance, the state held before the scan until
+     the first one), so that the batch is weighted like the chain's samples of
+     pi; loss = -(residence-weighted mean of log q),
+  4. backpropagates through tnmc_logq_backward and takes a backtracking
+     gradient-ascent step on the FP32 tensors.
+The weighted mean estimates E_pi[log q] = -KL(pi || q) - H(pi): maximising it
+moves q towards pi.  (Weighting each accepted proposal once instead would favour
+the states q already over-proposes.)
 Tuning changes q while the chain runs (an adaptive chain): use it during burn-in
 and freeze q for production sampling.
 """
@@ -16,36 +24,77 @@ import torch
 from . import autograd, binding
 
 
-def tune(env, steps=50, proposals=16384, chains=64, lr=1e-3, seed=0, min_batch=64, log=None):
-    """Run `steps` tuning steps; returns a list of per-step records."""
-    params = binding.get_params(env).clone().requires_grad_(True)
-    opt = torch.optim.Adam([params], lr=lr)
+def residence_weights(acc):
+    """acc: bool/uint8 [C, T] accept flags of one scan.  Returns (w_acc [C, T], w_held [C]):
+    how many of the T proposals each accepted proposal, and the state held before the
+    scan, stayed the chain's state (they sum to T per chain)."""
+    A = acc.bool()
+    C, T = A.shape
+    j = torch.arange(T, device=A.device).expand(C, T)
+    pos = torch.where(A, j, torch.full_like(j, T))
+    after = torch.cat([pos[:, 1:], torch.full((C, 1), T, dtype=pos.dtype, device=A.device)], dim=1)
+    nxt = after.flip(1).cummin(dim=1).values.flip(1)        # first acceptance after j (or T)
+    w_acc = torch.where(A, nxt - j, torch.zeros_like(j))
+    w_held = pos.min(dim=1).values                          # first acceptance (or T)
+    return w_acc, w_held
+
+
+def tune(env, steps=50, proposals=16384, chains=64, step=1e-2, seed=0, min_batch=64, max_backtrack=8, log=None):
+    """Run `steps` tuning steps; returns a list of per-step records.
+
+    Gradient ascent with backtracking on each step's batch: the update
+    params + lr * grad is kept only if the batch's weighted mean log q does not
+    drop and no batch state gets q = 0 (the clamped conditionals make the
+    objective fall off a cliff where a weight crosses zero, which a fixed step
+    can jump over); otherwise lr is halved and the update retried.  A kept step
+    grows lr by 1.25.  The first lr moves the parameters by `step` of their norm.
+    """
+    params = binding.get_params(env).clone()
     T = max(1, proposals // chains)
     B = chains * T
     chain = binding.init_chains(env, chains, seed=seed, precision="f32")
+    lr = None
     hist = []
     for it in range(steps):
         torch.cuda.synchronize()
         t0 = time.time()
-        binding.set_params(env, params.detach())
+        binding.set_params(env, params)
         chain[1].copy_(binding.logq(env, chain[0], precision="f32")[0])      # cached log q under the new q
+        held, held_lq = chain[0].clone(), chain[1].clone()
         sp, lq, E, fl = binding.sample(env, B, seed=seed + 1, sample_offset=it * B, precision="f32")
         acc = binding.mh_step(env, chains, T, (sp, lq, E), chain, seed=seed + 2, step_offset=it * T)
-        idx = torch.nonzero(acc, as_tuple=False).flatten()
+        w_acc, w_held = residence_weights(acc.view(chains, T))
+        idx = torch.nonzero(w_acc.flatten(), as_tuple=False).flatten()
+        hidx = torch.nonzero(w_held * torch.isfinite(held_lq), as_tuple=False).flatten()   # not a start outside q
         rate = idx.numel() / B
-        loss_v = float("nan")
+        rec = {"step": it, "acceptance": rate, "accepted": int(idx.numel()), "loss": float("nan"), "lr": lr,
+               "kept": False}
         if idx.numel() >= min_batch:
-            batch = sp.index_select(0, idx)
-            loss = -autograd.logq(params, env, batch).mean()
-            opt.zero_grad()
-            loss.backward()
-            opt.step()
-            loss_v = float(loss.item())
+            batch = torch.cat([sp.index_select(0, idx), held.index_select(0, hidx)])
+            w = torch.cat([w_acc.flatten().index_select(0, idx), w_held.index_select(0, hidx)]).to(torch.float64)
+            w = w / w.sum()
+            p = params.clone().requires_grad_(True)
+            f = (w * autograd.logq(p, env, batch)).sum()
+            (g,) = torch.autograd.grad(f, p)
+            f = float(f.item())
+            rec["loss"] = -f
+            if lr is None:
+                lr = step * float(params.norm()) / max(float(g.norm()), 1e-30)
+            for _ in range(max_backtrack):
+                cand = params + lr * g
+                binding.set_params(env, cand)
+                fc = float((w * binding.logq(env, batch, precision="f32")[0]).sum().item())
+                if fc == fc and fc > -float("inf") and fc >= f:
+                    params = cand
+                    rec.update(kept=True, loss_after=-fc)
+                    lr *= 1.25
+                    break
+                lr *= 0.5
+            rec["lr"] = lr
         torch.cuda.synchronize()
-        rec = {"step": it, "acceptance": rate, "accepted": int(idx.numel()), "loss": loss_v,
-               "seconds": time.time() - t0}
+        rec["seconds"] = time.time() - t0
         hist.append(rec)
         if log:
             log(rec)
-    binding.set_params(env, params.detach())
+    binding.set_params(env, params)
     return hist

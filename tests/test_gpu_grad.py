@@ -100,11 +100,26 @@ def test_gradient_identities_at_config4_size(B):
 
 
 def test_tuning_raises_mean_logq(B):
-    """A few steps of gradient ascent raise the mean log q of accepted samples."""
+    """Tuning steps raise the residence-weighted mean log q of the chain's states on each
+    kept step and, judged exactly on a 4x4 lattice (all 65536 states), raise E_pi[log q]
+    without losing acceptance."""
+    from oracle import exact
     from paper_2104_13264_gb300 import tuning
-    inst = instances.villain(8, 8, 1.5, 2)
+    inst = instances.villain(4, 4, 1.5, 2)
+    S, _, pi, _ = exact.boltzmann(inst.Jh, inst.Jv, inst.h, inst.beta)
+    St = torch.from_numpy(S).cuda()
     env = B.Env.from_instance(inst, precisions=("f64", "f32"))
-    hist = tuning.tune(env, steps=12, proposals=16384, chains=64, lr=2e-2, seed=5, min_batch=16)
-    losses = [h["loss"] for h in hist if h["loss"] == h["loss"]]
-    assert len(losses) >= 6, hist
-    assert np.mean(losses[-3:]) < np.mean(losses[:3]), hist
+
+    def judge():
+        lq = B.logq(env, St, precision="f32")[0].cpu().numpy()
+        return float((pi * lq).sum()), exact.independence_acceptance(pi, np.exp(lq))
+
+    f0, a0 = judge()
+    hist = tuning.tune(env, steps=20, proposals=65536, chains=64, seed=5, min_batch=16)
+    kept = [h for h in hist if h["kept"]]
+    assert len(kept) >= 10, hist
+    assert all(h["loss_after"] <= h["loss"] for h in kept)
+    f1, a1 = judge()
+    # E_pi[log q] is the objective; the acceptance follows it only on average (on the
+    # oracle the same procedure moves it 0.897 -> 0.901 with +-0.003 step-to-step noise)
+    assert f1 > f0 and a1 > a0 - 0.003, (f0, f1, a0, a1)
