@@ -32,6 +32,8 @@ CONFIGS = {
                                        "beta=2.0, 4096 proposals each, one persistent graph-captured launch"),
     "c4": ("config4", 16384, 64, "f32", "64x64 fully frustrated, beta=1.5, chi=32, B=16384"),
     "c5": ("config5", 1 << 20, 1024, "bf16", "256x256 ferromagnet, beta=0.4407, chi=64, B=2^20"),
+    "c5p": ("config5_strip", 65536, 64, "bf16", "16x256 ferromagnet strip (Lx, beta, chi of the 256x256 case), "
+                                               "B=65536: profiling case of the sampler kernels"),
 }
 
 

@@ -121,6 +121,12 @@ def config5():
     return ferromagnet(256, 256, 0.4407, 64)
 
 
+def config5_strip(Ly=16):
+    """The first Ly rows' worth of the 256-wide critical ferromagnet (same Lx, beta, chi):
+    a lattice small enough to build in seconds, for profiling the sampler kernels."""
+    return ferromagnet(Ly, 256, 0.4407, 64)
+
+
 def random_tensors(shapes, seed=0, positive=True):
     """Seeded random tensors of the given shapes (inputs for gradient checks)."""
     rng = np.random.default_rng([seed, 11])
