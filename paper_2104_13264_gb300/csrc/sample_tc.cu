@@ -2,24 +2,25 @@
 // App. A) for sm_103a: tcgen05.mma with the accumulator in TMEM, environment tiles
 // streamed into shared memory by bulk async copies, FP32 accumulation.
 //
-// A CTA owns a tile of 128 samples: thread t = sample t = TMEM lane t (four warps,
-// warp w reads lanes 32w..32w+31).  Per site one UMMA 128 x 128 x 64 forms, for all
-// samples at once,
+// A CTA owns a tile of 128 samples (UMMA M = 128): sample t is TMEM lane t.  Per
+// site one UMMA 128 x 128 x 64 forms, for all samples at once,
 //   right sweep  D[t][(s, a)] = sum_b R_{c+1}[t][b] M_c[a][s][b]   -> R_c = f(-) D(-) + f(+) D(+)
 //   left sweep   D[t][(s, b)] = sum_a Lambda_c[t][a] M_c[a][s][b]  -> U[s] = D(s)
-// with the vectors (A operand, 128 x 64 BF16) in shared memory and the environment
-// tile (B operand, 128 x 64 BF16) loaded from a pre-swizzled copy of the
-// environment.  The epilogue (one thread per sample) combines the field factors,
-// rescales by a power of two, draws the spin from Philox, accumulates log q and the
-// energy, and writes the next A operand.
+// with the vectors (A operand, 128 x 64) in shared memory and the environment tile
+// (B operand, 128 x 64) loaded from a pre-swizzled copy of the environment.  Both
+// operands are BF16 hi + lo pairs; the three products hi*hi + lo*hi + hi*lo keep
+// about 16 significant bits (the lo*lo term is below that).
 //
-// The left sweep needs R_{c+1} in the reverse of the order the right sweep makes it.
-// A full per-sample stack (Lx x 64 values per row) does not fit on chip, so the right
-// sweep stores a checkpoint every KS sites in global scratch and the left sweep
-// recomputes each segment of KS vectors from its checkpoint just before using it
-// (three contraction passes per row instead of two; the scratch, about 0.5 MB per
-// CTA at Lx = 256, stays in L2).  Recomputed vectors equal the first pass's
-// bit for bit (same operands, same instructions).
+// 256 threads: thread (t, h) = (tid % 128, tid / 128) runs the epilogue of sample t
+// for the components k in [32h, 32h + 32) -- warps w and w + 4 read the same TMEM
+// lanes (lane quadrant w % 4) at different columns.  The two halves exchange their
+// partial dot products and maxima through shared memory under a named barrier per
+// warp pair, and take identical decisions from identical sums.
+//
+// The left sweep needs R_{c+1} in the reverse of the order the right sweep makes it:
+// the right sweep writes every R_c to a per-CTA stack in global memory (Lx x 32 KB per
+// tile and row), and the left sweep reads it back, the load issued before it waits on
+// the UMMA.  Steps per row: (Lx - 1) right + Lx left.
 #include <math.h>
 
 #include "common.cuh"
@@ -29,14 +30,13 @@ namespace tnmc {
 namespace {
 
 constexpr int kTile = 128;          // samples per CTA (UMMA M)
+constexpr int kThreads = 256;       // two epilogue threads per sample
 constexpr int kK = 64;              // padded bond dimension (UMMA K per site)
 constexpr int kN = 128;             // 2 x 64 outputs (UMMA N)
-constexpr int kKS = 8;              // checkpoint stride (sites)
 constexpr int kStages = 2;          // environment-tile ring (one step of look-ahead)
 constexpr uint32_t kTileBytes = kN * kK * 2;   // 16 KiB: one BF16 operand tile
 constexpr uint32_t kStageBytes = 2 * kTileBytes;   // hi + lo tiles of one (r, c)
 constexpr uint32_t kVecBytes = kTile * kK * 2;  // 16 KiB (one BF16 A operand)
-constexpr uint32_t kRowF32 = kK;                // floats per scratch row
 constexpr uint32_t kPollLimit = 1u << 24;
 
 struct TcArgs {
@@ -54,55 +54,17 @@ struct TcArgs {
   double* logq;
   double* energy;
   int32_t* flags;
-  float* scratch;            // per CTA: (nchk + KS + 1) rows-blocks of 128 x 64 FP32
-  int nchk;                  // Lx / KS + 1
+  float4* stack;             // per CTA: [Lx][2 halves][8 chunks][128 samples] float4
 };
-
-// Position of step i of a row: type (0 = right sweep, 1 = left sweep) and site c.
-struct StepPos {
-  int left, c, seg_lo, seg_hi, first_of_seg;
-};
-
-__device__ inline StepPos decode_step(int i, int Lx) {
-  StepPos p{0, 0, 0, 0, 0};
-  if (i < Lx - 1) {
-    p.left = 0;
-    p.c = Lx - 1 - i;
-    p.seg_lo = -1;
-    return p;
-  }
-  const int i2 = i - (Lx - 1);
-  const int full = 2 * kKS - 1;
-  int lo = (i2 / full) * kKS;
-  int r2 = i2 - (lo / kKS) * full;
-  const int hi = min(lo + kKS, Lx);
-  const int len = hi - lo;
-  p.seg_lo = lo;
-  p.seg_hi = hi;
-  p.first_of_seg = (r2 == 0);
-  if (r2 < len - 1) {
-    p.left = 0;
-    p.c = hi - 1 - r2;
-  } else {
-    p.left = 1;
-    p.c = lo + (r2 - (len - 1));
-  }
-  return p;
-}
-
-__device__ inline int steps_per_row(int Lx) {
-  const int nseg = (Lx + kKS - 1) / kKS;
-  return (Lx - 1) + (2 * Lx - nseg);
-}
 
 __device__ inline float pow2f(int e) { return __int_as_float((e + 127) << 23); }   // 2^e, |e| < 127
 __device__ inline int ilogb_f(float x) { return ((__float_as_int(x) >> 23) & 0xff) - 127; }   // x normal, > 0
 
-// Split 64 FP32 values into BF16 hi + lo and store them as row t of the two
-// swizzled A operands (the vector operand carries about 16 significant bits).
-__device__ inline void store_split(unsigned char* sHi, unsigned char* sLo, int t, const float* v) {
+// Split 32 FP32 values (components 32h .. 32h+31) into BF16 hi + lo and store them in
+// row t of the two swizzled A operands.
+__device__ inline void store_split_half(unsigned char* sHi, unsigned char* sLo, int t, int h, const float* v) {
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
+  for (int j = 0; j < 4; ++j) {
     uint32_t wh[4], wl[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -112,31 +74,23 @@ __device__ inline void store_split(unsigned char* sHi, unsigned char* sLo, int t
       wh[q] = *reinterpret_cast<const uint32_t*>(&h2);
       wl[q] = *reinterpret_cast<const uint32_t*>(&l2);
     }
-    const uint32_t off = umma::sw128_offset(t, 8 * j);
+    const uint32_t off = umma::sw128_offset(t, 32 * h + 8 * j);
     *reinterpret_cast<uint4*>(sHi + off) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
     *reinterpret_cast<uint4*>(sLo + off) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
   }
 }
 
-__device__ inline void store_row(float* g, const float* v) {
+// e_0 restricted to this thread's half
+__device__ inline void unit_half(float* v, int h) {
 #pragma unroll
-  for (int j = 0; j < 16; ++j) reinterpret_cast<float4*>(g)[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
-}
-__device__ inline void load_row(const float* g, float* v) {
-#pragma unroll
-  for (int j = 0; j < 16; ++j) {
-    const float4 x = reinterpret_cast<const float4*>(g)[j];
-    v[4 * j] = x.x; v[4 * j + 1] = x.y; v[4 * j + 2] = x.z; v[4 * j + 3] = x.w;
-  }
-}
-__device__ inline void unit_row(float* v) {
-#pragma unroll
-  for (int q = 0; q < 64; ++q) v[q] = (q == 0) ? 1.0f : 0.0f;
+  for (int q = 0; q < 32; ++q) v[q] = (h == 0 && q == 0) ? 1.0f : 0.0f;
 }
 
-__device__ inline void prefetch_l1(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
+__device__ inline void pair_sync(int warp) {
+  asm volatile("bar.sync %0, 64;" ::"r"(1 + (warp & 3)) : "memory");
+}
 
-__global__ void __launch_bounds__(kTile, 2) sample_tc_kernel(TcArgs a) {
+__global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   unsigned char* sHi = base;
@@ -144,30 +98,25 @@ __global__ void __launch_bounds__(kTile, 2) sample_tc_kernel(TcArgs a) {
   unsigned char* sB = base + 2 * kVecBytes;
   uint64_t* bars = reinterpret_cast<uint64_t*>(sB + kStages * kStageBytes);  // full[kStages], mma
   uint32_t* misc = reinterpret_cast<uint32_t*>(bars + kStages + 1);         // [0] tmem base, [1] abort
+  float* xw = reinterpret_cast<float*>(misc + 4);                             // [2 halves][2][128] partial w
+  float* xm = xw + 4 * kTile;                                                  // [2 halves][128] partial max
   const int Lx = a.e.Lx, Ly = a.e.Ly;
   const int W = (Lx + 31) >> 5;
-  uint32_t* bits_prev = misc + 4;
+  uint32_t* bits_prev = reinterpret_cast<uint32_t*>(xm + 2 * kTile);
   uint32_t* bits_cur = bits_prev + W * kTile;
-  float* rowc = reinterpret_cast<float*>(bits_cur + W * kTile);   // per-row caches: fe (2Lx), h, Jh, Jv
-  float* fe_row = rowc;
-  float* h_row = rowc + 2 * Lx;
-  float* jh_row = h_row + Lx;
-  float* jv_row = jh_row + Lx;
 
-  const int t = threadIdx.x, warp = t >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int t = tid & (kTile - 1), h = tid >> 7;
   const int64_t ntiles = (a.B + kTile - 1) / kTile;
-  const int S = steps_per_row(Lx);
+  const int S = 2 * Lx - 1;
   const int64_t my_tiles = (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x;
   const int64_t total_steps = my_tiles * (int64_t)Ly * S;
   const int n = Lx * Ly;
-  float* chk = a.scratch + (size_t)blockIdx.x * (a.nchk + kKS + 1) * kTile * kRowF32;
-  float* seg = chk + (size_t)a.nchk * kTile * kRowF32;
-  float* stash = seg + (size_t)kKS * kTile * kRowF32;
-  float* my_stash = stash + (size_t)t * kRowF32;
+  float4* stk = a.stack + (size_t)blockIdx.x * Lx * (2 * 8 * kTile) + (size_t)h * (8 * kTile) + t;
   const uint32_t idesc = umma::idesc_bf16_f32(kTile, kN);
 
   if (warp == 0) umma::tmem_alloc(umma::smem_u32(&misc[0]), kN);
-  if (t == 0) {
+  if (tid == 0) {
     for (int s = 0; s <= kStages; ++s) umma::mbar_init(umma::smem_u32(&bars[s]), 1);
     umma::fence_mbar_init();
     misc[1] = 0;
@@ -176,13 +125,14 @@ __global__ void __launch_bounds__(kTile, 2) sample_tc_kernel(TcArgs a) {
   __syncthreads();
   umma::fence_after_sync();
   const uint32_t tmem = misc[0];
-  const uint32_t tlane = tmem + ((uint32_t)(32 * warp) << 16);
+  const uint32_t tlane = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + 32 * h;
 
   // producer position (row, step within the row) of the next tile to load
   int prod_r = 0, prod_i = 0;
   auto next_tile = [&]() -> const __nv_bfloat16* {
-    const StepPos p = decode_step(prod_i, Lx);
-    const __nv_bfloat16* T = (p.left ? a.TL : a.TR) + ((size_t)prod_r * Lx + p.c) * (2 * kN * kK);
+    const bool left = prod_i >= Lx - 1;
+    const int c = left ? prod_i - (Lx - 1) : Lx - 1 - prod_i;
+    const __nv_bfloat16* T = (left ? a.TL : a.TR) + ((size_t)prod_r * Lx + c) * (2 * kN * kK);
     if (++prod_i == S) {
       prod_i = 0;
       if (++prod_r == Ly) prod_r = 0;
@@ -190,7 +140,7 @@ __global__ void __launch_bounds__(kTile, 2) sample_tc_kernel(TcArgs a) {
     return T;
   };
   int64_t issued = 0;
-  if (t == 0) {
+  if (tid == 0) {
     const int64_t pro = total_steps < kStages - 1 ? total_steps : (int64_t)(kStages - 1);
     for (; issued < pro; ++issued) {
       const uint32_t st = (uint32_t)(issued % kStages);
@@ -201,26 +151,22 @@ __global__ void __launch_bounds__(kTile, 2) sample_tc_kernel(TcArgs a) {
 
   int64_t g = 0;
   bool abort = false;
-  float v[64];
   for (int64_t tile = blockIdx.x; tile < ntiles && !abort; tile += gridDim.x) {
     const int64_t b = tile * kTile + t;
     const bool active = b < a.B;
     const uint64_t sample = a.offset + (uint64_t)b;
     double lq = 0.0, E = 0.0;
     int flag = 0;
-    for (int wd = 0; wd < W; ++wd) bits_prev[wd * kTile + t] = 0u;
+    if (h == 0)
+      for (int wd = 0; wd < W; ++wd) bits_prev[wd * kTile + t] = 0u;
     uint64_t pair_word = 0;
     int64_t pair_id = -1;
     for (int r = 0; r < Ly && !abort; ++r) {
-      // row caches
-      for (int c = t; c < Lx; c += kTile) {
-        fe_row[2 * c] = a.fe[((size_t)r * Lx + c) * 2];
-        fe_row[2 * c + 1] = a.fe[((size_t)r * Lx + c) * 2 + 1];
-        h_row[c] = a.h32[r * Lx + c];
-        jh_row[c] = (c < Lx - 1) ? a.Jh32[r * (Lx - 1) + c] : 0.0f;
-        jv_row[c] = (r > 0) ? a.Jv32[(r - 1) * Lx + c] : 0.0f;
-      }
-      if (a.spins_in) {
+      const float* fe_row = a.fe + (size_t)r * Lx * 2;
+      const float* h_row = a.h32 + (size_t)r * Lx;
+      const float* jh_row = a.Jh32 + (size_t)r * (Lx - 1);
+      const float* jv_row = a.Jv32 + (size_t)(r > 0 ? r - 1 : 0) * Lx;
+      if (a.spins_in && h == 0) {
         for (int wd = 0; wd < W; ++wd) bits_cur[wd * kTile + t] = 0u;
         if (active) {
           const int8_t* src = a.spins_in + (size_t)b * n + (size_t)r * Lx;
@@ -228,13 +174,11 @@ __global__ void __launch_bounds__(kTile, 2) sample_tc_kernel(TcArgs a) {
             if (src[c] > 0) bits_cur[(c >> 5) * kTile + t] |= 1u << (c & 31);
         }
       }
-      // row start: R_{Lx} = e_0 (or, for Lx = 1, straight into the left sweep)
-      unit_row(v);
-      if (Lx > 1) {
-        store_split(sHi, sLo, t, v);
-      } else {
-        store_row(seg + (size_t)t * kRowF32, v);   // R_1 = e_0 in slot 0
-        store_split(sHi, sLo, t, v);                // Lambda_0 = e_0
+      // row start: A = R_{Lx} = e_0 (Lx > 1) or Lambda_0 = e_0 (Lx = 1)
+      {
+        float v[32];
+        unit_half(v, h);
+        store_split_half(sHi, sLo, t, h, v);
       }
       float prod = 1.0f;
       int pexp = 0;
@@ -244,10 +188,10 @@ __global__ void __launch_bounds__(kTile, 2) sample_tc_kernel(TcArgs a) {
       umma::fence_before_sync();
       __syncthreads();
       for (int i = 0; i < S; ++i, ++g) {
-        const StepPos p = decode_step(i, Lx);
-        const int c = p.c;
+        const bool left = i >= Lx - 1;
+        const int c = left ? i - (Lx - 1) : Lx - 1 - i;
         umma::fence_after_sync();
-        if (t == 0) {
+        if (tid == 0) {
           const uint32_t st = (uint32_t)(g % kStages);
           if (!umma::mbar_wait(umma::smem_u32(&bars[st]), (uint32_t)((g / kStages) & 1), kPollLimit)) {
             set_status(a.e.status, TNMC_E_TIMEOUT);
@@ -257,7 +201,6 @@ __global__ void __launch_bounds__(kTile, 2) sample_tc_kernel(TcArgs a) {
             const uint64_t al = umma::sw128_desc(umma::smem_u32(sLo));
             const uint64_t bh = umma::sw128_desc(umma::smem_u32(sB + st * kStageBytes));
             const uint64_t bl = umma::sw128_desc(umma::smem_u32(sB + st * kStageBytes + kTileBytes));
-            // (A_hi + A_lo)(B_hi + B_lo) without the A_lo B_lo term (below 2^-16 relative)
 #pragma unroll
             for (int k = 0; k < kK / 16; ++k) umma::mma_bf16(tmem, ah + 2 * k, bh + 2 * k, idesc, k > 0);
 #pragma unroll
@@ -276,14 +219,23 @@ __global__ void __launch_bounds__(kTile, 2) sample_tc_kernel(TcArgs a) {
         }
         // work that does not need the accumulator, overlapped with the UMMA
         const bool up = (r > 0) && ((bits_prev[(c >> 5) * kTile + t] >> (c & 31)) & 1u);
-        const float fsame = fe_row[2 * c + 1], fdiff = fe_row[2 * c];
-        const float fm = (r == 0) ? 1.0f : (up ? fdiff : fsame);
-        const float fp = (r == 0) ? 1.0f : (up ? fsame : fdiff);
-        const float* Rn = p.left ? seg + ((size_t)(c - p.seg_lo) * kTile + t) * kRowF32 : nullptr;
+        const float fsame = (r == 0) ? 1.0f : fe_row[2 * c + 1];
+        const float fdiff = (r == 0) ? 1.0f : fe_row[2 * c];
+        const float fm = up ? fdiff : fsame;   // s = -1
+        const float fp = up ? fsame : fdiff;   // s = +1
         uint64_t x = 0;
-        if (p.left) {
-          prefetch_l1(Rn);
-          prefetch_l1(Rn + 32);
+        float rv[32];   // this half of R_{c+1}: loads in flight while the UMMA runs
+        if (left) {
+          if (c + 1 < Lx) {
+            const float4* src = stk + (size_t)(c + 1) * (2 * 8 * kTile);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const float4 q4 = src[j * kTile];
+              rv[4 * j] = q4.x; rv[4 * j + 1] = q4.y; rv[4 * j + 2] = q4.z; rv[4 * j + 3] = q4.w;
+            }
+          } else {
+            unit_half(rv, h);
+          }
           if (!a.spins_in) {
             const int64_t site = (int64_t)r * Lx + c;
             if ((site & 1) && (site >> 1) == pair_id) {
@@ -304,46 +256,45 @@ __global__ void __launch_bounds__(kTile, 2) sample_tc_kernel(TcArgs a) {
           misc[1] = 1;
         }
         umma::fence_after_sync();
-        if (!p.left) {
-          // ---- right-sweep epilogue: R_c = f(-) D(-, a) + f(+) D(+, a) ----
+        uint32_t u0[32], u1[32];
+        umma::tmem_ld32_issue(tlane, u0);        // s = -1, this half
+        umma::tmem_ld32_issue(tlane + 64, u1);   // s = +1, this half
+        umma::tmem_wait_ld();
+        umma::tmem_hold(u0);
+        umma::tmem_hold(u1);
+        float v[32];
+        if (!left) {
+          // ---- right-sweep epilogue: R_c = f(-) D(-, a) + f(+) D(+, a), rescaled ----
           float mx = 0.0f;
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            float y0[32], y1[32];
-            umma::tmem_ld32(tlane + 32 * h, y0);
-            umma::tmem_ld32(tlane + 64 + 32 * h, y1);
-#pragma unroll
-            for (int q = 0; q < 32; ++q) {
-              v[32 * h + q] = fm * y0[q] + fp * y1[q];
-              mx = fmaxf(mx, fabsf(v[32 * h + q]));
-            }
+          for (int q = 0; q < 32; ++q) {
+            v[q] = fm * __uint_as_float(u0[q]) + fp * __uint_as_float(u1[q]);
+            mx = fmaxf(mx, fabsf(v[q]));
           }
+          xm[h * kTile + t] = mx;
+          pair_sync(warp);
+          mx = fmaxf(xm[t], xm[kTile + t]);
           const float sc = (mx > 0.0f && mx < INFINITY) ? pow2f(-ilogb_f(mx)) : 1.0f;
 #pragma unroll
-          for (int q = 0; q < 64; ++q) v[q] *= sc;
-          store_split(sHi, sLo, t, v);
-          if (p.seg_lo < 0) {
-            if (c % kKS == 0) store_row(chk + ((size_t)(c / kKS) * kTile + t) * kRowF32, v);
-          } else {
-            store_row(seg + ((size_t)(c - p.seg_lo - 1) * kTile + t) * kRowF32, v);
-          }
+          for (int q = 0; q < 32; ++q) v[q] *= sc;
+          float4* dst = stk + (size_t)c * (2 * 8 * kTile);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) dst[j * kTile] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+          if (c == 1) unit_half(v, h);           // the left sweep starts from Lambda_0 = e_0
+          store_split_half(sHi, sLo, t, h, v);
         } else {
           // ---- left-sweep epilogue: w(s) = f(s) <U[s], R_{c+1}>, draw, Lambda_{c+1} ----
-          float w0 = 0.0f, w1 = 0.0f;
+          float p0 = 0.0f, p1 = 0.0f;
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            float u0[32], u1[32];
-            umma::tmem_ld32(tlane + 32 * h, u0);
-            umma::tmem_ld32(tlane + 64 + 32 * h, u1);
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              const float4 rv = reinterpret_cast<const float4*>(Rn)[8 * h + j];
-              w0 = fmaf(u0[4 * j], rv.x, w0); w0 = fmaf(u0[4 * j + 1], rv.y, w0);
-              w0 = fmaf(u0[4 * j + 2], rv.z, w0); w0 = fmaf(u0[4 * j + 3], rv.w, w0);
-              w1 = fmaf(u1[4 * j], rv.x, w1); w1 = fmaf(u1[4 * j + 1], rv.y, w1);
-              w1 = fmaf(u1[4 * j + 2], rv.z, w1); w1 = fmaf(u1[4 * j + 3], rv.w, w1);
-            }
+          for (int q = 0; q < 32; ++q) {
+            p0 = fmaf(__uint_as_float(u0[q]), rv[q], p0);
+            p1 = fmaf(__uint_as_float(u1[q]), rv[q], p1);
           }
+          xw[(2 * h) * kTile + t] = p0;
+          xw[(2 * h + 1) * kTile + t] = p1;
+          pair_sync(warp);
+          float w0 = xw[t] + xw[2 * kTile + t];            // half 0 + half 1, same order in both
+          float w1 = xw[kTile + t] + xw[3 * kTile + t];
           w0 = fmaxf(w0 * fm, 0.0f);
           w1 = fmaxf(w1 * fp, 0.0f);
           const float tot = w0 + w1;
@@ -351,68 +302,40 @@ __global__ void __launch_bounds__(kTile, 2) sample_tc_kernel(TcArgs a) {
           const float pplus = bad ? 0.5f : w1 / tot;
           const float pminus = bad ? 0.5f : w0 / tot;
           bool plus;
-          if (a.spins_in) {
-            plus = (bits_cur[(c >> 5) * kTile + t] >> (c & 31)) & 1u;
-          } else {
-            plus = draw_plus(pplus, x);
-            if (plus) bits_cur[(c >> 5) * kTile + t] |= 1u << (c & 31);
-            else bits_cur[(c >> 5) * kTile + t] &= ~(1u << (c & 31));
-          }
-          prod *= plus ? pplus : pminus;
-          if (prod < 0x1.0p-60f && prod > 0.0f) {
-            prod *= 0x1.0p60f;
-            pexp -= 60;
-          }
-          flag |= bad ? TNMC_FLAG_NUMERIC : 0;
-          {
+          if (a.spins_in) plus = (bits_cur[(c >> 5) * kTile + t] >> (c & 31)) & 1u;
+          else plus = draw_plus(pplus, x);
+          if (h == 0) {
+            if (!a.spins_in) {
+              if (plus) bits_cur[(c >> 5) * kTile + t] |= 1u << (c & 31);
+              else bits_cur[(c >> 5) * kTile + t] &= ~(1u << (c & 31));
+            }
+            prod *= plus ? pplus : pminus;
+            if (prod < 0x1.0p-60f && prod > 0.0f) {
+              prod *= 0x1.0p60f;
+              pexp -= 60;
+            }
+            flag |= bad ? TNMC_FLAG_NUMERIC : 0;
             float loc = h_row[c];
             if (c > 0) loc += jh_row[c - 1] * (s_left ? 1.0f : -1.0f);
             if (r > 0) loc += jv_row[c] * (up ? 1.0f : -1.0f);
             Erow -= (plus ? 1.0f : -1.0f) * loc;
+            s_left = plus;
           }
-          s_left = plus;
-          // Lambda_{c+1} = f(s) U[s], rescaled.  tcgen05.ld takes one TMEM address per
-          // warp, so both halves are read and each thread keeps its own spin's half.
+          // Lambda_{c+1} = f(s) U[s], rescaled
           const float fs = plus ? fp : fm;
           float mx = 0.0f;
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            float um[32], upl[32];
-            umma::tmem_ld32(tlane + 32 * h, um);
-            umma::tmem_ld32(tlane + 64 + 32 * h, upl);
-#pragma unroll
-            for (int q = 0; q < 32; ++q) {
-              v[32 * h + q] = (plus ? upl[q] : um[q]) * fs;
-              mx = fmaxf(mx, fabsf(v[32 * h + q]));
-            }
+          for (int q = 0; q < 32; ++q) {
+            v[q] = __uint_as_float(plus ? u1[q] : u0[q]) * fs;
+            mx = fmaxf(mx, fabsf(v[q]));
           }
+          xm[h * kTile + t] = mx;
+          pair_sync(warp);
+          mx = fmaxf(xm[t], xm[kTile + t]);
           const float sc = (mx > 0.0f && mx < INFINITY) ? pow2f(-ilogb_f(mx)) : 1.0f;
 #pragma unroll
-          for (int q = 0; q < 64; ++q) v[q] *= sc;
-          store_split(sHi, sLo, t, v);
-          if (c == p.seg_hi - 1 && c < Lx - 1) store_row(my_stash, v);   // Lambda survives the next recompute
-        }
-        // operand of the next step when a chain starts or resumes
-        if (i + 1 < S) {
-          const StepPos nx = decode_step(i + 1, Lx);
-          if (nx.left && !(nx.first_of_seg)) {
-            const float* Rnx = seg + ((size_t)(nx.c - nx.seg_lo) * kTile + t) * kRowF32;
-            prefetch_l1(Rnx);
-            prefetch_l1(Rnx + 32);
-          }
-          if (nx.first_of_seg) {
-            // R_hi: its checkpoint, or e_0 at the right end, into segment slot hi - lo - 1
-            if (nx.seg_hi >= Lx) unit_row(v);
-            else load_row(chk + ((size_t)(nx.seg_hi / kKS) * kTile + t) * kRowF32, v);
-            store_row(seg + ((size_t)(nx.seg_hi - nx.seg_lo - 1) * kTile + t) * kRowF32, v);
-            if (!nx.left) store_split(sHi, sLo, t, v);
-          }
-          if (nx.left && (!p.left || nx.first_of_seg)) {
-            // Lambda resumes: e_0 for the first segment, else the stash
-            if (nx.seg_lo == 0) unit_row(v);
-            else load_row(my_stash, v);
-            store_split(sHi, sLo, t, v);
-          }
+          for (int q = 0; q < 32; ++q) v[q] *= sc;
+          store_split_half(sHi, sLo, t, h, v);
         }
         umma::fence_proxy_async();
         umma::fence_before_sync();
@@ -423,31 +346,33 @@ __global__ void __launch_bounds__(kTile, 2) sample_tc_kernel(TcArgs a) {
         }
       }
       // end of row: log q, energy, spins; this row becomes the previous row
-      lq += log((double)prod) + (double)pexp * 0.69314718055994530942;
-      E += (double)Erow;
-      if (active && a.spins_out && !a.spins_in) {
-        int8_t* dst = a.spins_out + (size_t)b * n + (size_t)r * Lx;
-        if ((Lx & 15) == 0 && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
-          for (int c0 = 0; c0 < Lx; c0 += 16) {
-            const uint32_t wb = bits_cur[(c0 >> 5) * kTile + t] >> (c0 & 31);
-            uint32_t wv[4];
+      if (h == 0) {
+        lq += log((double)prod) + (double)pexp * 0.69314718055994530942;
+        E += (double)Erow;
+        if (active && a.spins_out && !a.spins_in) {
+          int8_t* dst = a.spins_out + (size_t)b * n + (size_t)r * Lx;
+          if ((Lx & 15) == 0 && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
+            for (int c0 = 0; c0 < Lx; c0 += 16) {
+              const uint32_t wb = bits_cur[(c0 >> 5) * kTile + t] >> (c0 & 31);
+              uint32_t wv[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              uint32_t word = 0;
+              for (int q = 0; q < 4; ++q) {
+                uint32_t word = 0;
 #pragma unroll
-              for (int z = 0; z < 4; ++z) word |= (uint32_t)(((wb >> (4 * q + z)) & 1u) ? 0x01u : 0xFFu) << (8 * z);
-              wv[q] = word;
+                for (int z = 0; z < 4; ++z) word |= (uint32_t)(((wb >> (4 * q + z)) & 1u) ? 0x01u : 0xFFu) << (8 * z);
+                wv[q] = word;
+              }
+              *reinterpret_cast<uint4*>(dst + c0) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
             }
-            *reinterpret_cast<uint4*>(dst + c0) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+          } else {
+            for (int c = 0; c < Lx; ++c) dst[c] = ((bits_cur[(c >> 5) * kTile + t] >> (c & 31)) & 1u) ? 1 : -1;
           }
-        } else {
-          for (int c = 0; c < Lx; ++c) dst[c] = ((bits_cur[(c >> 5) * kTile + t] >> (c & 31)) & 1u) ? 1 : -1;
         }
+        for (int wd = 0; wd < W; ++wd) bits_prev[wd * kTile + t] = bits_cur[wd * kTile + t];
       }
-      for (int wd = 0; wd < W; ++wd) bits_prev[wd * kTile + t] = bits_cur[wd * kTile + t];
-      __syncthreads();   // the row caches are rewritten for the next row
+      __syncthreads();   // bits_prev is read by both halves in the next row
     }
-    if (active && !abort) {
+    if (h == 0 && active && !abort) {
       a.logq[b] = flag ? -INFINITY : lq;
       a.energy[b] = E;
       if (a.flags) a.flags[b] = flag;
@@ -455,7 +380,7 @@ __global__ void __launch_bounds__(kTile, 2) sample_tc_kernel(TcArgs a) {
     }
   }
   // teardown: let copies still in flight land (bounded), then free TMEM
-  if (t == 0) {
+  if (tid == 0) {
     for (int64_t q = g; q < issued; ++q)
       (void)umma::mbar_wait(umma::smem_u32(&bars[q % kStages]), (uint32_t)((q / kStages) & 1), kPollLimit);
   }
@@ -528,7 +453,7 @@ tnmc_status tnmc_launch_sample_tc(const tnmc_env* env, int64_t B, uint64_t seed,
   }
   const int W = (d.Lx + 31) / 32;
   const size_t smem = 1024 + 2 * kVecBytes + kStages * kStageBytes + (kStages + 1) * 8 + 16 +
-                      (size_t)2 * W * kTile * sizeof(uint32_t) + (size_t)5 * d.Lx * sizeof(float);
+                      (size_t)6 * kTile * sizeof(float) + (size_t)2 * W * kTile * sizeof(uint32_t);
   int dev = 0, nsm = 0, max_optin = 0;
   TNMC_CUDA_TRY(cudaGetDevice(&dev));
   TNMC_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -541,7 +466,7 @@ tnmc_status tnmc_launch_sample_tc(const tnmc_env* env, int64_t B, uint64_t seed,
   TNMC_CUDA_TRY(cudaFuncSetAttribute(sample_tc_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
                                      (int)cudaSharedmemCarveoutMaxShared));
   int per_sm = 0;
-  TNMC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sample_tc_kernel, kTile, smem));
+  TNMC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sample_tc_kernel, kThreads, smem));
   {
     // cross-check the occupancy query against the shared-memory budget of an SM
     int smem_sm = 0, regs_sm = 0;
@@ -550,7 +475,7 @@ tnmc_status tnmc_launch_sample_tc(const tnmc_env* env, int64_t B, uint64_t seed,
     cudaFuncAttributes fa;
     TNMC_CUDA_TRY(cudaFuncGetAttributes(&fa, sample_tc_kernel));
     const int by_smem = smem_sm / (int)(smem + 1024);
-    const int by_regs = regs_sm / (((fa.numRegs + 7) & ~7) * kTile);
+    const int by_regs = regs_sm / (((fa.numRegs + 7) & ~7) * kThreads);
     const int est = by_smem < by_regs ? by_smem : by_regs;
     if (est > per_sm) per_sm = est;
   }
@@ -559,8 +484,7 @@ tnmc_status tnmc_launch_sample_tc(const tnmc_env* env, int64_t B, uint64_t seed,
   const int64_t ntiles = (B + kTile - 1) / kTile;
   int64_t grid = (int64_t)nsm * per_sm;
   if (grid > ntiles) grid = ntiles;
-  const int nchk = d.Lx / kKS + 1;
-  const size_t need = (size_t)grid * (nchk + kKS + 1) * kTile * kRowF32 * sizeof(float);
+  const size_t need = (size_t)grid * d.Lx * kTile * kK * sizeof(float);
   tnmc_env* me = const_cast<tnmc_env*>(env);
   if (me->scratch.bytes < need) {
     if (me->scratch.ptr) TNMC_CUDA_TRY(cudaFreeAsync(me->scratch.ptr, stream));
@@ -591,9 +515,8 @@ tnmc_status tnmc_launch_sample_tc(const tnmc_env* env, int64_t B, uint64_t seed,
   a.logq = logq;
   a.energy = energy;
   a.flags = flags;
-  a.scratch = static_cast<float*>(me->scratch.ptr);
-  a.nchk = nchk;
-  sample_tc_kernel<<<(unsigned)grid, kTile, smem, stream>>>(a);
+  a.stack = static_cast<float4*>(me->scratch.ptr);
+  sample_tc_kernel<<<(unsigned)grid, kThreads, smem, stream>>>(a);
   TNMC_CUDA_TRY(cudaGetLastError());
   return TNMC_OK;
 }
