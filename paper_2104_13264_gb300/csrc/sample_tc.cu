@@ -226,6 +226,13 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
         uint64_t x = 0;
         float rv[32];   // this half of R_{c+1}: loads in flight while the UMMA runs
         if (left) {
+          if (c + 2 < Lx) {
+            // R_{c+2} into L2 one step ahead: each lane fetches one of its warp's 32 lines
+            const int lane = tid & 31;
+            const float4* pf = stk - t + 32 * (warp & 3) + (size_t)(c + 2) * (2 * 8 * kTile) +
+                               (size_t)(lane >> 2) * kTile + 8 * (lane & 3);
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(pf));
+          }
           if (c + 1 < Lx) {
             const float4* src = stk + (size_t)(c + 1) * (2 * 8 * kTile);
 #pragma unroll
