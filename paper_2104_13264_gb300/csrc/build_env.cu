@@ -317,7 +317,7 @@ __device__ inline void tournament(int t, int i, int N, int& p, int& q) {
 
 // One-sided Jacobi (Hestenes): orthogonalise the m <= 128 rows (length n, stride
 // ld) of J.  Round-robin pairing; a group of L lanes owns one pair, with L chosen
-// so that all m/2 pairs of a round run at once on the 256 threads.  Squared row
+// so that all m/2 pairs of a round run at once on the CTA's threads.  Squared row
 // norms d[] are maintained through the exact update alpha' = alpha - t gamma,
 // beta' = beta + t gamma and recomputed at the start of every sweep.  A pair is
 // rotated while |gamma| > tol sqrt(alpha beta), tol = 1e-13 (above the rounding
@@ -330,9 +330,9 @@ constexpr double kNullRel = 1e-13;
 __device__ void jacobi_rows(double* J, int m, int n, int ld, double* d, int* flag) {
   const int N = m + (m & 1);
   const int npairs = N / 2;
-  // four lanes per pair: the FP64 pipe, not the thread count, bounds this loop,
-  // and the per-pair scalar work is repeated on every lane of a group
-  const int L = 4;
+  // blockDim.x / 64 lanes per pair (a power of two): all m/2 <= 64 pairs of a round
+  // at once; the per-pair scalar work is repeated on every lane of a group
+  const int L = blockDim.x / 64;
   const int grp = threadIdx.x / L, gl = threadIdx.x % L;
   for (int sweep = 0; sweep < 40; ++sweep) {
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
@@ -349,7 +349,7 @@ __device__ void jacobi_rows(double* J, int m, int n, int ld, double* d, int* fla
       {
         // every lane runs the group shuffles below (full-warp masks); groups beyond
         // the round's pairs only contribute zeros.  m <= 128 gives at most 64 pairs,
-        // one per group of four lanes on 256 threads.
+        // one per group of lanes.
         int p = m, q = m;
         if (grp < npairs) tournament(t, grp, N, p, q);
         const bool live = p < m && q < m;
@@ -775,6 +775,86 @@ __device__ inline int z2_col(int s, int j, int Dr, int er) {
   return Dr + (s ? 0 : er) + (j - ns0);           // tau = 1, x in sector 1 - s
 }
 
+// Both parity sectors of a site at once: the first half of the threads orthogonalises
+// the m0 rows of J0, the second half the m1 rows of J1 (m0, m1 <= 64; same n, ld), each
+// with the rounds, tolerances and arithmetic of jacobi_rows (blockDim.x / 64 lanes per
+// pair, a power of two).  Sweeps continue until neither
+// sector rotates; a converged sector's extra sweep rotates nothing.
+__device__ void jacobi_rows2(double* J0, int m0, double* J1, int m1, int n, int ld, double* d0, double* d1,
+                             int* flag) {
+  const int half = blockDim.x >> 1;          // threads per sector
+  const int sec = threadIdx.x >= half;
+  const int lt = threadIdx.x - sec * half;
+  double* J = sec ? J1 : J0;
+  double* d = sec ? d1 : d0;
+  const int m = sec ? m1 : m0;
+  const int N = m + (m & 1);
+  const int npairs = N / 2;
+  const int Nmax = max(m0 + (m0 & 1), m1 + (m1 & 1));
+  const int L = half / 32;                   // lanes per pair: all 32 pairs of a round at once
+  const int grp = lt / L, gl = lt % L;
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    for (int i = lt; i < m; i += half) {
+      double s = 0.0;
+      for (int x = 0; x < n; ++x) s += J[(size_t)i * ld + x] * J[(size_t)i * ld + x];
+      d[i] = s;
+    }
+    if (threadIdx.x == 0) {
+      flag[0] = 0;
+      flag[2] = 0;
+    }
+    __syncthreads();
+    double dmax = 0.0;
+    for (int i = 0; i < m; ++i) dmax = fmax(dmax, d[i]);
+    const double dnull = kNullRel * kNullRel * dmax;
+    for (int t = 0; t < Nmax - 1; ++t) {
+      {
+        // groups beyond this sector's pairs (or rounds) only contribute zeros to the shuffles
+        int p = m, q = m;
+        if (grp < npairs && t < N - 1) tournament(t, grp, N, p, q);
+        const bool live = p < m && q < m;
+        double ga = 0.0;
+        double* rp = J + (size_t)(live ? p : 0) * ld;
+        double* rq = J + (size_t)(live ? q : 0) * ld;
+        if (live)
+          for (int x = gl; x < n; x += L) ga += rp[x] * rq[x];
+        for (int o = 1; o < L; o <<= 1) ga += __shfl_xor_sync(0xffffffffu, ga, o);
+        if (live) {
+          const double al = d[p], be = d[q];
+          if (ga != 0.0 && al > dnull && be > dnull && ga * ga > kJacobiTol * kJacobiTol * al * be) {
+            float zeta = (float)(be - al) / (2.0f * (float)ga);
+            if (!isfinite(zeta)) zeta = (float)((be - al) / (2.0 * ga));
+            float tf;
+            if (fabsf(zeta) > 1e18f) tf = 0.5f / zeta;
+            else tf = (zeta >= 0.0f ? 1.0f : -1.0f) / (fabsf(zeta) + sqrtf(1.0f + zeta * zeta));
+            const double tt = (double)tf;
+            const double x = fma(tt, tt, 1.0);
+            double cs = (double)rsqrtf((float)x);
+            cs = cs * fma(-0.5 * x, cs * cs, 1.5);
+            cs = cs * fma(-0.5 * x, cs * cs, 1.5);
+            const double sn = cs * tt;
+            for (int xx = gl; xx < n; xx += L) {
+              const double u = rp[xx], v = rq[xx];
+              rp[xx] = cs * u - sn * v;
+              rq[xx] = sn * u + cs * v;
+            }
+            if (gl == 0) {
+              const double c2 = cs * cs;
+              d[p] = c2 * fma(tt * tt, be, fma(-2.0 * tt, ga, al));
+              d[q] = c2 * fma(tt * tt, al, fma(2.0 * tt, ga, be));
+              flag[2 * sec] = 1;
+            }
+          }
+        }
+      }
+      __syncthreads();
+    }
+    const int rotated = flag[0] | flag[2];
+    __syncthreads();
+    if (!rotated) break;
+  }
+}
+
 __device__ double svd_sweep_z2(const BuildArgs& a, ShZ2& sh, int r) {
   const int Lx = a.Lx, P = a.P;
   const size_t slot_sz = (size_t)8 * P * P;
@@ -800,8 +880,12 @@ __device__ double svd_sweep_z2(const BuildArgs& a, ShZ2& sh, int r) {
       J[l * ld + j] = A[(size_t)l * 2 * Dr + col];
     }
     __syncthreads();
-    if (el > 0) jacobi_rows(J, el, n, ld, nrm, sh.flag);
-    if (Dl - el > 0) jacobi_rows(J + (size_t)el * ld, Dl - el, n, ld, nrm + el, sh.flag);
+    if (el <= 64 && Dl - el <= 64) {
+      jacobi_rows2(J, el, J + (size_t)el * ld, Dl - el, n, ld, nrm, nrm + el, sh.flag);
+    } else {
+      if (el > 0) jacobi_rows(J, el, n, ld, nrm, sh.flag);
+      if (Dl - el > 0) jacobi_rows(J + (size_t)el * ld, Dl - el, n, ld, nrm + el, sh.flag);
+    }
     for (int i = w; i < Dl; i += kWarps) {
       double sq = 0.0;
       for (int x = lane; x < n; x += 32) sq += J[i * ld + x] * J[i * ld + x];
