@@ -126,7 +126,7 @@ def dist_setup(args):
 def run_tnmc(args):
     import torch
     from paper_2104_13264_gb300 import binding as Bd
-    from paper_2104_13264_gb300 import instances
+    from paper_2104_13264_gb300 import instances, replicas
 
     world, rank, local = dist_setup(args)
     torch.cuda.set_device(local)
@@ -145,9 +145,45 @@ def run_tnmc(args):
     dev = torch.device("cuda", local)
 
     t0 = time.time()
-    env = Bd.Env.from_instance(inst, precisions=tuple(sorted({"f64", prec})))
+    env = Bd.Env.from_instance(inst, precisions=tuple(sorted({"f64", prec} | ({"f32"} if args.tune_steps else set()))))
     info = env.info()
     env_build_s = time.time() - t0
+    tuning = None
+    if args.tune_steps:
+        # gradient ascent of the FP32 tensors on the chain states' mean log q (hand-written
+        # backward of log q); the timed sampling below then uses the tuned FP32 copy
+        from paper_2104_13264_gb300 import tuning as tn
+        assert prec == "f32", "tuning acts on the FP32 sampler copy"
+        torch.cuda.synchronize()
+        t1 = time.time()
+        hist = tn.tune(env, steps=args.tune_steps, proposals=B, chains=C, seed=args.seed + 11)
+        torch.cuda.synchronize()
+        tune_s = time.time() - t1
+        # backward-kernel time on one batch of B proposals (CUDA events on its stream)
+        sp_b = Bd.sample(env, B, seed=args.seed + 13, precision="f32")[0]
+        wts = torch.full((B,), 1.0 / B, dtype=torch.float32, device=dev)
+        Bd.logq_backward(env, sp_b, wts)
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record()
+        Bd.logq_backward(env, sp_b, wts)
+        g1.record()
+        torch.cuda.synchronize()
+        bw_ms = g0.elapsed_time(g1)
+        bw_flops = 3 * algorithmic_flops(inst) * B
+        smmax_t = float(load_peaks()[0].get("sm_max_mhz", 2070.0))
+        peak_t = 152 * 128 * 2 * smmax_t * 1e6 / 1e12
+        del sp_b
+        tuning = {"steps": args.tune_steps, "seconds": round(tune_s, 3),
+                  "acceptance_first3": round(statistics.mean(h["acceptance"] for h in hist[:3]), 5),
+                  "acceptance_last3": round(statistics.mean(h["acceptance"] for h in hist[-3:]), 5),
+                  "kept_steps": sum(1 for h in hist if h["kept"]),
+                  "backward_ms": round(bw_ms, 3),
+                  "backward_roofline": {"bound": "alu", "unit": "TFLOP/s",
+                                        "achieved": round(bw_flops / (bw_ms / 1e3) / 1e12, 3),
+                                        "peak": round(peak_t, 3),
+                                        "frac": round(bw_flops / (bw_ms / 1e3) / 1e12 / peak_t, 5),
+                                        "flop_per_launch": bw_flops,
+                                        "note": "3x the forward's algorithmic FLOPs (recompute + reverse sweeps)"}}
 
     spins = torch.empty((B, inst.Ly, inst.Lx), dtype=torch.int8, device=dev)
     logq = torch.empty(B, dtype=torch.float64, device=dev)
@@ -166,7 +202,7 @@ def run_tnmc(args):
     ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
 
     def step(i, timed):
-        off = (rank * B) + (i * B * world)
+        off = replicas.sample_offset(rank, world, i, B)
         if flush is not None:
             flush.fill_(i & 0xFF)
         if timed:
@@ -175,8 +211,9 @@ def run_tnmc(args):
                   out=(spins, logq, energy, flags), stream=stream)
         if timed:
             ev_m[i].record(stream)
-        Bd.mh_step(env, C, T, (spins, logq, energy), chain, seed=args.seed + 1, step_offset=i * T,
-                   accepted=acc, n_accepted=nacc, stream=stream)
+        Bd.mh_step(env, C, T, (spins, logq, energy), chain, seed=args.seed + 1,
+                   step_offset=replicas.mh_step_offset(rank, world, i, T), accepted=acc, n_accepted=nacc,
+                   stream=stream)
         if timed:
             ev_e[i].record(stream)
 
@@ -205,14 +242,7 @@ def run_tnmc(args):
     total_ms = t_start.elapsed_time(t_end)
     sample_ms = [ev_s[i].elapsed_time(ev_m[i]) for i in range(args.steps)]
     n_accepted = int(nacc.item())
-    if pg:
-        t = torch.tensor([total_ms, float(n_accepted)], dtype=torch.float64, device=dev)
-        mx = t.clone()
-        pg.all_reduce(mx, op=pg.ReduceOp.MAX)
-        sm = t.clone()
-        pg.all_reduce(sm, op=pg.ReduceOp.SUM)
-        total_ms = float(mx[0])
-        n_accepted = int(sm[1])
+    total_ms, n_accepted = replicas.reduce_timing(total_ms, n_accepted, pg, dev)
     status = env.status()
 
     # end-to-end through the public API with host buffers: chain states live in pinned
@@ -234,10 +264,11 @@ def run_tnmc(args):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for i in range(e2e_steps):
-        off = (rank * B) + ((args.steps + i) * B * world)
+        off = replicas.sample_offset(rank, world, args.steps + i, B)
         dchain[0].copy_(hs, non_blocking=True); dchain[1].copy_(hlq, non_blocking=True); dchain[2].copy_(hE, non_blocking=True)
         Bd.sample(env, B, seed=args.seed, sample_offset=off, precision=prec, out=(spins, logq, energy, flags), stream=stream)
-        Bd.mh_step(env, C, T, (spins, logq, energy), dchain, seed=args.seed + 1, step_offset=(args.steps + i) * T,
+        Bd.mh_step(env, C, T, (spins, logq, energy), dchain, seed=args.seed + 1,
+                   step_offset=replicas.mh_step_offset(rank, world, args.steps + i, T),
                    accepted=acc, n_accepted=nacc_e, stream=stream)
         hs.copy_(dchain[0], non_blocking=True); hlq.copy_(dchain[1], non_blocking=True); hE.copy_(dchain[2], non_blocking=True)
         hacc.copy_(acc, non_blocking=True)
@@ -301,6 +332,7 @@ def run_tnmc(args):
                    "l2": "flushed (256 MiB write between steps)" if flush is not None else "outputs > L2"},
         "proposals_per_s": round(props_s, 3), "acceptance": round(acc_rate, 5),
         "env_build_s": round(env_build_s, 3), "logZ": info["logZ"], "device_status": status,
+        "tuning": tuning,
         "roofline": roof, "cpu_baseline": cpu, "plain_f64": plain,
         "e2e": {"value": round(e2e_acc / (e2e_ms * e2e_steps / 1e3), 3) if e2e_ms > 0 else None,
                 "unit": "accepted samples/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
@@ -320,7 +352,7 @@ def run_batched(args):
     import torch
     from paper_2104_13264_gb300 import batched
     from paper_2104_13264_gb300 import binding as Bd
-    from paper_2104_13264_gb300 import instances
+    from paper_2104_13264_gb300 import instances, replicas
 
     world, rank, local = dist_setup(args)
     torch.cuda.set_device(local)
@@ -379,13 +411,7 @@ def run_batched(args):
         torch.cuda.synchronize()
         ks.append(k0.elapsed_time(k1))
     kern_s = statistics.mean(ks) / 1e3
-    if pg:
-        t = torch.tensor([total_ms, float(n_accepted)], dtype=torch.float64, device=dev)
-        mx = t.clone()
-        pg.all_reduce(mx, op=pg.ReduceOp.MAX)
-        sm = t.clone()
-        pg.all_reduce(sm, op=pg.ReduceOp.SUM)
-        total_ms, n_accepted = float(mx[0]), int(sm[1])
+    total_ms, n_accepted = replicas.reduce_timing(total_ms, n_accepted, pg, dev)
 
     # end to end: chain states of every instance uploaded from pinned host memory before,
     # and read back with the accept flags after, each graph replay
@@ -672,6 +698,8 @@ def main():
     ap.add_argument("--cpu-batch", type=int, default=0)
     ap.add_argument("--plain-batch", type=int, default=2 * 152 * 64)   # one full wave of the FP64 kernel
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--tune-steps", type=int, default=0,
+                    help="tuning steps of the FP32 tensors before the timed sampling (the 64x64 Villain case uses 50)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
