@@ -19,8 +19,10 @@
 //
 // The left sweep needs R_{c+1} in the reverse of the order the right sweep makes it:
 // the right sweep writes every R_c to a per-CTA stack in global memory (Lx x 32 KB per
-// tile and row), and the left sweep reads it back, the load issued before it waits on
-// the UMMA.  Steps per row: (Lx - 1) right + Lx left.
+// tile and row), and the left sweep brings it back with one 32 KB bulk copy into shared
+// memory, issued with the step's UMMA (and prefetched into L2 a step earlier).  The
+// environment tile of the next step is copied as soon as the UMMA has read the current
+// one, while the epilogue runs.  Steps per row: (Lx - 1) right + Lx left.
 #include <math.h>
 
 #include "common.cuh"
@@ -33,10 +35,10 @@ constexpr int kTile = 128;          // samples per CTA (UMMA M)
 constexpr int kThreads = 256;       // two epilogue threads per sample
 constexpr int kK = 64;              // padded bond dimension (UMMA K per site)
 constexpr int kN = 128;             // 2 x 64 outputs (UMMA N)
-constexpr int kStages = 2;          // environment-tile ring (one step of look-ahead)
 constexpr uint32_t kTileBytes = kN * kK * 2;   // 16 KiB: one BF16 operand tile
 constexpr uint32_t kStageBytes = 2 * kTileBytes;   // hi + lo tiles of one (r, c)
 constexpr uint32_t kVecBytes = kTile * kK * 2;  // 16 KiB (one BF16 A operand)
+constexpr uint32_t kRBytes = kTile * kK * 4;    // 32 KiB: R_{c+1} of the tile, FP32
 constexpr uint32_t kPollLimit = 1u << 24;
 
 struct TcArgs {
@@ -95,9 +97,10 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   unsigned char* sHi = base;
   unsigned char* sLo = base + kVecBytes;
-  unsigned char* sB = base + 2 * kVecBytes;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + kStages * kStageBytes);  // full[kStages], mma
-  uint32_t* misc = reinterpret_cast<uint32_t*>(bars + kStages + 1);         // [0] tmem base, [1] abort
+  unsigned char* sB = base + 2 * kVecBytes;                                   // environment tile (hi, lo)
+  const float4* sR = reinterpret_cast<const float4*>(sB + kStageBytes);      // [2][8][128] float4
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + kStageBytes + kRBytes);  // [0] tile, [1] UMMA, [2] R
+  uint32_t* misc = reinterpret_cast<uint32_t*>(bars + 3);                    // [0] tmem base, [1] abort
   float* xw = reinterpret_cast<float*>(misc + 4);                             // [2 halves][2][128] partial w
   float* xm = xw + 4 * kTile;                                                  // [2 halves][128] partial max
   const int Lx = a.e.Lx, Ly = a.e.Ly;
@@ -112,12 +115,13 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
   const int64_t my_tiles = (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x;
   const int64_t total_steps = my_tiles * (int64_t)Ly * S;
   const int n = Lx * Ly;
-  float4* stk = a.stack + (size_t)blockIdx.x * Lx * (2 * 8 * kTile) + (size_t)h * (8 * kTile) + t;
+  float4* stk_cta = a.stack + (size_t)blockIdx.x * Lx * (2 * 8 * kTile);
+  float4* stk = stk_cta + (size_t)h * (8 * kTile) + t;
   const uint32_t idesc = umma::idesc_bf16_f32(kTile, kN);
 
   if (warp == 0) umma::tmem_alloc(umma::smem_u32(&misc[0]), kN);
   if (tid == 0) {
-    for (int s = 0; s <= kStages; ++s) umma::mbar_init(umma::smem_u32(&bars[s]), 1);
+    for (int s = 0; s < 3; ++s) umma::mbar_init(umma::smem_u32(&bars[s]), 1);
     umma::fence_mbar_init();
     misc[1] = 0;
   }
@@ -139,14 +143,13 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
     }
     return T;
   };
-  int64_t issued = 0;
-  if (tid == 0) {
-    const int64_t pro = total_steps < kStages - 1 ? total_steps : (int64_t)(kStages - 1);
-    for (; issued < pro; ++issued) {
-      const uint32_t st = (uint32_t)(issued % kStages);
-      umma::mbar_expect_tx(umma::smem_u32(&bars[st]), kStageBytes);
-      umma::bulk_g2s(umma::smem_u32(sB + st * kStageBytes), next_tile(), kStageBytes, umma::smem_u32(&bars[st]));
-    }
+  int64_t issued = 0;               // environment tiles copied (thread 0)
+  uint32_t r_issued = 0, r_done = 0; // R copies issued / waited for (thread 0)
+  uint32_t nr = 0;                   // R copies consumed (every thread)
+  if (tid == 0 && total_steps > 0) {
+    umma::mbar_expect_tx(umma::smem_u32(&bars[0]), kStageBytes);
+    umma::bulk_g2s(umma::smem_u32(sB), next_tile(), kStageBytes, umma::smem_u32(&bars[0]));
+    issued = 1;
   }
 
   int64_t g = 0;
@@ -190,17 +193,23 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
       for (int i = 0; i < S; ++i, ++g) {
         const bool left = i >= Lx - 1;
         const int c = left ? i - (Lx - 1) : Lx - 1 - i;
+        const bool rcopy = left && c + 1 < Lx;
         umma::fence_after_sync();
         if (tid == 0) {
-          const uint32_t st = (uint32_t)(g % kStages);
-          if (!umma::mbar_wait(umma::smem_u32(&bars[st]), (uint32_t)((g / kStages) & 1), kPollLimit)) {
+          if (rcopy) {   // R_{c+1} of the whole tile: the buffer was last read before the step's barrier
+            umma::mbar_expect_tx(umma::smem_u32(&bars[2]), kRBytes);
+            umma::bulk_g2s(umma::smem_u32(sR), stk_cta + (size_t)(c + 1) * (2 * 8 * kTile), kRBytes,
+                           umma::smem_u32(&bars[2]));
+            ++r_issued;
+          }
+          if (!umma::mbar_wait(umma::smem_u32(&bars[0]), (uint32_t)(g & 1), kPollLimit)) {
             set_status(a.e.status, TNMC_E_TIMEOUT);
             misc[1] = 1;
           } else {
             const uint64_t ah = umma::sw128_desc(umma::smem_u32(sHi));
             const uint64_t al = umma::sw128_desc(umma::smem_u32(sLo));
-            const uint64_t bh = umma::sw128_desc(umma::smem_u32(sB + st * kStageBytes));
-            const uint64_t bl = umma::sw128_desc(umma::smem_u32(sB + st * kStageBytes + kTileBytes));
+            const uint64_t bh = umma::sw128_desc(umma::smem_u32(sB));
+            const uint64_t bl = umma::sw128_desc(umma::smem_u32(sB + kTileBytes));
 #pragma unroll
             for (int k = 0; k < kK / 16; ++k) umma::mma_bf16(tmem, ah + 2 * k, bh + 2 * k, idesc, k > 0);
 #pragma unroll
@@ -208,14 +217,7 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
 #pragma unroll
             for (int k = 0; k < kK / 16; ++k) umma::mma_bf16(tmem, ah + 2 * k, bl + 2 * k, idesc, 1);
           }
-          umma::mma_commit(umma::smem_u32(&bars[kStages]));
-          if (issued < total_steps) {
-            const uint32_t st2 = (uint32_t)(issued % kStages);
-            umma::mbar_expect_tx(umma::smem_u32(&bars[st2]), kStageBytes);
-            umma::bulk_g2s(umma::smem_u32(sB + st2 * kStageBytes), next_tile(), kStageBytes,
-                           umma::smem_u32(&bars[st2]));
-            ++issued;
-          }
+          umma::mma_commit(umma::smem_u32(&bars[1]));
         }
         // work that does not need the accumulator, overlapped with the UMMA
         const bool up = (r > 0) && ((bits_prev[(c >> 5) * kTile + t] >> (c & 31)) & 1u);
@@ -224,7 +226,7 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
         const float fm = up ? fdiff : fsame;   // s = -1
         const float fp = up ? fsame : fdiff;   // s = +1
         uint64_t x = 0;
-        float rv[32];   // this half of R_{c+1}: loads in flight while the UMMA runs
+        float rv[32];   // this half of R_{c+1}
         if (left) {
           if (c + 2 < Lx) {
             // R_{c+2} into L2 one step ahead: each lane fetches one of its warp's 32 lines
@@ -232,16 +234,6 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
             const float4* pf = stk - t + 32 * (warp & 3) + (size_t)(c + 2) * (2 * 8 * kTile) +
                                (size_t)(lane >> 2) * kTile + 8 * (lane & 3);
             asm volatile("prefetch.global.L2 [%0];" ::"l"(pf));
-          }
-          if (c + 1 < Lx) {
-            const float4* src = stk + (size_t)(c + 1) * (2 * 8 * kTile);
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              const float4 q4 = src[j * kTile];
-              rv[4 * j] = q4.x; rv[4 * j + 1] = q4.y; rv[4 * j + 2] = q4.z; rv[4 * j + 3] = q4.w;
-            }
-          } else {
-            unit_half(rv, h);
           }
           if (!a.spins_in) {
             const int64_t site = (int64_t)r * Lx + c;
@@ -258,11 +250,17 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
             }
           }
         }
-        if (!umma::mbar_wait(umma::smem_u32(&bars[kStages]), (uint32_t)(g & 1), kPollLimit)) {
+        if (!umma::mbar_wait(umma::smem_u32(&bars[1]), (uint32_t)(g & 1), kPollLimit)) {
           set_status(a.e.status, TNMC_E_TIMEOUT);
           misc[1] = 1;
         }
         umma::fence_after_sync();
+        if (tid == 0 && issued < total_steps) {
+          // the UMMA has read the tile: the next step's tile lands while the epilogue runs
+          umma::mbar_expect_tx(umma::smem_u32(&bars[0]), kStageBytes);
+          umma::bulk_g2s(umma::smem_u32(sB), next_tile(), kStageBytes, umma::smem_u32(&bars[0]));
+          ++issued;
+        }
         uint32_t u0[32], u1[32];
         umma::tmem_ld32_issue(tlane, u0);        // s = -1, this half
         umma::tmem_ld32_issue(tlane + 64, u1);   // s = +1, this half
@@ -272,12 +270,13 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
         float v[32];
         if (!left) {
           // ---- right-sweep epilogue: R_c = f(-) D(-, a) + f(+) D(+, a), rescaled ----
-          float mx = 0.0f;
+          float m4[4] = {0.0f, 0.0f, 0.0f, 0.0f};   // four independent chains (max is exact)
 #pragma unroll
           for (int q = 0; q < 32; ++q) {
             v[q] = fm * __uint_as_float(u0[q]) + fp * __uint_as_float(u1[q]);
-            mx = fmaxf(mx, fabsf(v[q]));
+            m4[q & 3] = fmaxf(m4[q & 3], fabsf(v[q]));
           }
+          float mx = fmaxf(fmaxf(m4[0], m4[1]), fmaxf(m4[2], m4[3]));
           xm[h * kTile + t] = mx;
           pair_sync(warp);
           mx = fmaxf(xm[t], xm[kTile + t]);
@@ -291,12 +290,32 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
           store_split_half(sHi, sLo, t, h, v);
         } else {
           // ---- left-sweep epilogue: w(s) = f(s) <U[s], R_{c+1}>, draw, Lambda_{c+1} ----
-          float p0 = 0.0f, p1 = 0.0f;
+          if (rcopy) {
+            if (!umma::mbar_wait(umma::smem_u32(&bars[2]), nr & 1u, kPollLimit)) {
+              set_status(a.e.status, TNMC_E_TIMEOUT);
+              misc[1] = 1;
+            } else if (tid == 0) {
+              ++r_done;
+            }
+            ++nr;
+            const float4* src = sR + h * (8 * kTile) + t;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const float4 q4 = src[j * kTile];
+              rv[4 * j] = q4.x; rv[4 * j + 1] = q4.y; rv[4 * j + 2] = q4.z; rv[4 * j + 3] = q4.w;
+            }
+          } else {
+            unit_half(rv, h);
+          }
+          // partial dot products over this half, in four interleaved chains
+          float a0[4] = {0.0f, 0.0f, 0.0f, 0.0f}, a1[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
           for (int q = 0; q < 32; ++q) {
-            p0 = fmaf(__uint_as_float(u0[q]), rv[q], p0);
-            p1 = fmaf(__uint_as_float(u1[q]), rv[q], p1);
+            a0[q & 3] = fmaf(__uint_as_float(u0[q]), rv[q], a0[q & 3]);
+            a1[q & 3] = fmaf(__uint_as_float(u1[q]), rv[q], a1[q & 3]);
           }
+          const float p0 = (a0[0] + a0[1]) + (a0[2] + a0[3]);
+          const float p1 = (a1[0] + a1[1]) + (a1[2] + a1[3]);
           xw[(2 * h) * kTile + t] = p0;
           xw[(2 * h + 1) * kTile + t] = p1;
           pair_sync(warp);
@@ -330,12 +349,13 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
           }
           // Lambda_{c+1} = f(s) U[s], rescaled
           const float fs = plus ? fp : fm;
-          float mx = 0.0f;
+          float m4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
           for (int q = 0; q < 32; ++q) {
             v[q] = __uint_as_float(plus ? u1[q] : u0[q]) * fs;
-            mx = fmaxf(mx, fabsf(v[q]));
+            m4[q & 3] = fmaxf(m4[q & 3], fabsf(v[q]));
           }
+          float mx = fmaxf(fmaxf(m4[0], m4[1]), fmaxf(m4[2], m4[3]));
           xm[h * kTile + t] = mx;
           pair_sync(warp);
           mx = fmaxf(xm[t], xm[kTile + t]);
@@ -344,7 +364,8 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
           for (int q = 0; q < 32; ++q) v[q] *= sc;
           store_split_half(sHi, sLo, t, h, v);
         }
-        umma::fence_proxy_async();
+        // shared A operand and global stack writes become visible to the bulk copies and UMMAs
+        asm volatile("fence.proxy.async;" ::: "memory");
         umma::fence_before_sync();
         __syncthreads();
         if (misc[1]) {
@@ -389,7 +410,9 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
   // teardown: let copies still in flight land (bounded), then free TMEM
   if (tid == 0) {
     for (int64_t q = g; q < issued; ++q)
-      (void)umma::mbar_wait(umma::smem_u32(&bars[q % kStages]), (uint32_t)((q / kStages) & 1), kPollLimit);
+      (void)umma::mbar_wait(umma::smem_u32(&bars[0]), (uint32_t)(q & 1), kPollLimit);
+    for (uint32_t q = r_done; q < r_issued; ++q)
+      (void)umma::mbar_wait(umma::smem_u32(&bars[2]), q & 1u, kPollLimit);
   }
   umma::fence_before_sync();
   __syncthreads();
@@ -459,7 +482,7 @@ tnmc_status tnmc_launch_sample_tc(const tnmc_env* env, int64_t B, uint64_t seed,
     return TNMC_E_UNSUPPORTED;
   }
   const int W = (d.Lx + 31) / 32;
-  const size_t smem = 1024 + 2 * kVecBytes + kStages * kStageBytes + (kStages + 1) * 8 + 16 +
+  const size_t smem = 1024 + 2 * kVecBytes + kStageBytes + kRBytes + 3 * 8 + 16 +
                       (size_t)6 * kTile * sizeof(float) + (size_t)2 * W * kTile * sizeof(uint32_t);
   int dev = 0, nsm = 0, max_optin = 0;
   TNMC_CUDA_TRY(cudaGetDevice(&dev));
