@@ -226,7 +226,6 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
         const float fm = up ? fdiff : fsame;   // s = -1
         const float fp = up ? fsame : fdiff;   // s = +1
         uint64_t x = 0;
-        float rv[32];   // this half of R_{c+1}
         if (left) {
           if (c + 2 < Lx) {
             // R_{c+2} into L2 one step ahead: each lane fetches one of its warp's 32 lines
@@ -298,21 +297,21 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
               ++r_done;
             }
             ++nr;
-            const float4* src = sR + h * (8 * kTile) + t;
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              const float4 q4 = src[j * kTile];
-              rv[4 * j] = q4.x; rv[4 * j + 1] = q4.y; rv[4 * j + 2] = q4.z; rv[4 * j + 3] = q4.w;
-            }
-          } else {
-            unit_half(rv, h);
           }
-          // partial dot products over this half, in four interleaved chains
+          // partial dot products over this half, in four interleaved chains; R_{c+1} is
+          // read from the shared buffer chunk by chunk (e_0 at the right end of the row)
           float a0[4] = {0.0f, 0.0f, 0.0f, 0.0f}, a1[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+          const float4* src = sR + h * (8 * kTile) + t;
 #pragma unroll
-          for (int q = 0; q < 32; ++q) {
-            a0[q & 3] = fmaf(__uint_as_float(u0[q]), rv[q], a0[q & 3]);
-            a1[q & 3] = fmaf(__uint_as_float(u1[q]), rv[q], a1[q & 3]);
+          for (int j = 0; j < 8; ++j) {
+            float4 q4 = make_float4((h == 0 && j == 0) ? 1.0f : 0.0f, 0.0f, 0.0f, 0.0f);
+            if (rcopy) q4 = src[j * kTile];
+            const float r4[4] = {q4.x, q4.y, q4.z, q4.w};
+#pragma unroll
+            for (int z = 0; z < 4; ++z) {
+              a0[z] = fmaf(__uint_as_float(u0[4 * j + z]), r4[z], a0[z]);
+              a1[z] = fmaf(__uint_as_float(u1[4 * j + z]), r4[z], a1[z]);
+            }
           }
           const float p0 = (a0[0] + a0[1]) + (a0[2] + a0[3]);
           const float p1 = (a1[0] + a1[1]) + (a1[2] + a1[3]);
@@ -364,8 +363,10 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
           for (int q = 0; q < 32; ++q) v[q] *= sc;
           store_split_half(sHi, sLo, t, h, v);
         }
-        // shared A operand and global stack writes become visible to the bulk copies and UMMAs
-        asm volatile("fence.proxy.async;" ::: "memory");
+        // the shared A operand becomes visible to the UMMA; after a right step also the
+        // stack vector just written, to the bulk copy that reads it back
+        if (left) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        else asm volatile("fence.proxy.async;" ::: "memory");
         umma::fence_before_sync();
         __syncthreads();
         if (misc[1]) {
