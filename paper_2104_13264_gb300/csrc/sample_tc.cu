@@ -18,9 +18,10 @@
 // warp pair, and take identical decisions from identical sums.
 //
 // The left sweep needs R_{c+1} in the reverse of the order the right sweep makes it:
-// the right sweep writes every R_c to a per-CTA stack in global memory (Lx x 32 KB per
-// tile and row), and the left sweep brings it back with one 32 KB bulk copy into shared
-// memory, issued with the step's UMMA (and prefetched into L2 a step earlier).  The
+// the right sweep writes every R_c into a shared buffer, from which one 32 KB bulk store
+// moves it to a per-CTA stack in global memory (Lx x 32 KB per tile and row) during the
+// next step's UMMA; the left sweep brings it back with one bulk copy into the buffer,
+// issued with the step's UMMA (and prefetched into L2 a step earlier).  The
 // environment tile of the next step is copied as soon as the UMMA has read the current
 // one, while the epilogue runs.  Steps per row: (Lx - 1) right + Lx left.
 #include <math.h>
@@ -88,6 +89,18 @@ __device__ inline void unit_half(float* v, int h) {
   for (int q = 0; q < 32; ++q) v[q] = (h == 0 && q == 0) ? 1.0f : 0.0f;
 }
 
+// Bulk store shared -> global (one group per call), and the waits on it.
+__device__ inline void bulk_s2g(void* dst, uint32_t src_smem, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(src_smem), "r"(bytes)
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ inline void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ inline void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ inline void mbar_arrive(uint32_t mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+
 __device__ inline void pair_sync(int warp) {
   asm volatile("bar.sync %0, 64;" ::"r"(1 + (warp & 3)) : "memory");
 }
@@ -98,7 +111,7 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
   unsigned char* sHi = base;
   unsigned char* sLo = base + kVecBytes;
   unsigned char* sB = base + 2 * kVecBytes;                                   // environment tile (hi, lo)
-  const float4* sR = reinterpret_cast<const float4*>(sB + kStageBytes);      // [2][8][128] float4
+  float4* sR = reinterpret_cast<float4*>(sB + kStageBytes);                  // [2][8][128] float4
   uint64_t* bars = reinterpret_cast<uint64_t*>(sB + kStageBytes + kRBytes);  // [0] tile, [1] UMMA, [2] R
   uint32_t* misc = reinterpret_cast<uint32_t*>(bars + 3);                    // [0] tmem base, [1] abort
   float* xw = reinterpret_cast<float*>(misc + 4);                             // [2 halves][2][128] partial w
@@ -121,7 +134,9 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
 
   if (warp == 0) umma::tmem_alloc(umma::smem_u32(&misc[0]), kN);
   if (tid == 0) {
-    for (int s = 0; s < 3; ++s) umma::mbar_init(umma::smem_u32(&bars[s]), 1);
+    // the UMMA barrier completes on the commit and on thread 0, once the bulk store of the
+    // step (if any) has read the R buffer
+    for (int s = 0; s < 3; ++s) umma::mbar_init(umma::smem_u32(&bars[s]), s == 1 ? 2 : 1);
     umma::fence_mbar_init();
     misc[1] = 0;
   }
@@ -193,10 +208,12 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
       for (int i = 0; i < S; ++i, ++g) {
         const bool left = i >= Lx - 1;
         const int c = left ? i - (Lx - 1) : Lx - 1 - i;
-        const bool rcopy = left && c + 1 < Lx;
+        // R_1 is still in the buffer when the left sweep starts; later R_{c+1} come back by copy
+        const bool rcopy = left && c >= 1 && c + 1 < Lx;
         umma::fence_after_sync();
         if (tid == 0) {
           if (rcopy) {   // R_{c+1} of the whole tile: the buffer was last read before the step's barrier
+            bulk_wait_all();   // the stack stores of the right sweep have landed
             umma::mbar_expect_tx(umma::smem_u32(&bars[2]), kRBytes);
             umma::bulk_g2s(umma::smem_u32(sR), stk_cta + (size_t)(c + 1) * (2 * 8 * kTile), kRBytes,
                            umma::smem_u32(&bars[2]));
@@ -218,6 +235,13 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
             for (int k = 0; k < kK / 16; ++k) umma::mma_bf16(tmem, ah + 2 * k, bl + 2 * k, idesc, 1);
           }
           umma::mma_commit(umma::smem_u32(&bars[1]));
+          const int c_prev = Lx - i;   // site of the previous step when it was a right step
+          if (i >= 1 && i - 1 < Lx - 1 && c_prev >= 2) {
+            // R_{c_prev}, written to the buffer by the previous epilogue, goes to the stack
+            bulk_s2g(stk_cta + (size_t)c_prev * (2 * 8 * kTile), umma::smem_u32(sR), kRBytes);
+            bulk_wait_read();
+          }
+          mbar_arrive(umma::smem_u32(&bars[1]));
         }
         // work that does not need the accumulator, overlapped with the UMMA
         const bool up = (r > 0) && ((bits_prev[(c >> 5) * kTile + t] >> (c & 31)) & 1u);
@@ -282,7 +306,7 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
           const float sc = (mx > 0.0f && mx < INFINITY) ? pow2f(-ilogb_f(mx)) : 1.0f;
 #pragma unroll
           for (int q = 0; q < 32; ++q) v[q] *= sc;
-          float4* dst = stk + (size_t)c * (2 * 8 * kTile);
+          float4* dst = sR + h * (8 * kTile) + t;   // to the stack by a bulk store next step
 #pragma unroll
           for (int j = 0; j < 8; ++j) dst[j * kTile] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
           if (c == 1) unit_half(v, h);           // the left sweep starts from Lambda_0 = e_0
@@ -305,7 +329,7 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
             float4 q4 = make_float4((h == 0 && j == 0) ? 1.0f : 0.0f, 0.0f, 0.0f, 0.0f);
-            if (rcopy) q4 = src[j * kTile];
+            if (c + 1 < Lx) q4 = src[j * kTile];
             const float r4[4] = {q4.x, q4.y, q4.z, q4.w};
 #pragma unroll
             for (int z = 0; z < 4; ++z) {
@@ -363,10 +387,8 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
           for (int q = 0; q < 32; ++q) v[q] *= sc;
           store_split_half(sHi, sLo, t, h, v);
         }
-        // the shared A operand becomes visible to the UMMA; after a right step also the
-        // stack vector just written, to the bulk copy that reads it back
-        if (left) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        else asm volatile("fence.proxy.async;" ::: "memory");
+        // the shared A operand and R buffer become visible to the UMMA and the bulk store
+        umma::fence_proxy_async();
         umma::fence_before_sync();
         __syncthreads();
         if (misc[1]) {
@@ -414,6 +436,7 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
       (void)umma::mbar_wait(umma::smem_u32(&bars[0]), (uint32_t)(q & 1), kPollLimit);
     for (uint32_t q = r_done; q < r_issued; ++q)
       (void)umma::mbar_wait(umma::smem_u32(&bars[2]), q & 1u, kPollLimit);
+    bulk_wait_all();
   }
   umma::fence_before_sync();
   __syncthreads();
