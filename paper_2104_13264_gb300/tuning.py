@@ -9,8 +9,9 @@ the chain actually visits raises the acceptance.  Each tuning step
      proposal until the next acceptance, the state held before the scan until
      the first one), so that the batch is weighted like the chain's samples of
      pi; loss = -(residence-weighted mean of log q),
-  4. backpropagates through tnmc_logq_backward and takes a backtracking
-     gradient-ascent step on the FP32 tensors.
+  4. backpropagates through tnmc_logq_backward on one half of the chains and
+     takes a backtracking gradient-ascent step on the FP32 tensors, judged on the
+     other half.
 The weighted mean estimates E_pi[log q] = -KL(pi || q) - H(pi): maximising it
 moves q towards pi.  (Weighting each accepted proposal once instead would favour
 the states q already over-proposes.)
@@ -42,12 +43,15 @@ def residence_weights(acc):
 def tune(env, steps=50, proposals=16384, chains=64, step=1e-2, seed=0, min_batch=64, max_backtrack=8, log=None):
     """Run `steps` tuning steps; returns a list of per-step records.
 
-    Gradient ascent with backtracking on each step's batch: the update
-    params + lr * grad is kept only if the batch's weighted mean log q does not
-    drop and no batch state gets q = 0 (the clamped conditionals make the
-    objective fall off a cliff where a weight crosses zero, which a fixed step
-    can jump over); otherwise lr is halved and the update retried.  A kept step
-    grows lr by 1.25.  The first lr moves the parameters by `step` of their norm.
+    Gradient ascent with backtracking.  The chains are split in two halves: the
+    gradient comes from the states of the first half, and the update
+    params + lr * grad is kept only if the weighted mean log q of the second
+    half's states does not drop and none of them gets q = 0.  The clamped
+    conditionals make the objective fall off a cliff where a weight crosses
+    zero, which a fixed step can jump over; the held-out half keeps a step from
+    fitting one batch's noise.  Otherwise lr is halved and the update retried.
+    A kept step grows lr by 1.25.  The first lr moves the parameters by `step`
+    of their norm.  With one chain both roles use the same states.
     """
     params = binding.get_params(env).clone()
     T = max(1, proposals // chains)
@@ -64,29 +68,37 @@ def tune(env, steps=50, proposals=16384, chains=64, step=1e-2, seed=0, min_batch
         sp, lq, E, fl = binding.sample(env, B, seed=seed + 1, sample_offset=it * B, precision="f32")
         acc = binding.mh_step(env, chains, T, (sp, lq, E), chain, seed=seed + 2, step_offset=it * T)
         w_acc, w_held = residence_weights(acc.view(chains, T))
-        idx = torch.nonzero(w_acc.flatten(), as_tuple=False).flatten()
-        hidx = torch.nonzero(w_held * torch.isfinite(held_lq), as_tuple=False).flatten()   # not a start outside q
-        rate = idx.numel() / B
-        rec = {"step": it, "acceptance": rate, "accepted": int(idx.numel()), "loss": float("nan"), "lr": lr,
-               "kept": False}
-        if idx.numel() >= min_batch:
-            batch = torch.cat([sp.index_select(0, idx), held.index_select(0, hidx)])
-            w = torch.cat([w_acc.flatten().index_select(0, idx), w_held.index_select(0, hidx)]).to(torch.float64)
-            w = w / w.sum()
+        w_held = w_held * torch.isfinite(held_lq)                               # not a start outside q
+        rate = int(torch.count_nonzero(w_acc)) / B
+        rec = {"step": it, "acceptance": rate, "accepted": int(torch.count_nonzero(w_acc)), "loss": float("nan"),
+               "lr": lr, "kept": False}
+        half = chains // 2 if chains > 1 else chains
+        parts = []
+        for lo, hi in ((0, half), (half, chains) if chains > 1 else (0, chains)):
+            wa = w_acc[lo:hi].flatten()
+            idx = torch.nonzero(wa, as_tuple=False).flatten()
+            hidx = torch.nonzero(w_held[lo:hi], as_tuple=False).flatten()
+            batch = torch.cat([sp[lo * T:hi * T].index_select(0, idx), held[lo:hi].index_select(0, hidx)])
+            w = torch.cat([wa.index_select(0, idx), w_held[lo:hi].index_select(0, hidx)]).to(torch.float64)
+            parts.append((batch, w / w.sum().clamp_min(1), int(idx.numel())))
+        (b_fit, w_fit, n_fit), (b_val, w_val, _) = parts
+        if n_fit >= min_batch // 2 and w_val.sum() > 0:
             p = params.clone().requires_grad_(True)
-            f = (w * autograd.logq(p, env, batch)).sum()
+            f = (w_fit * autograd.logq(p, env, b_fit)).sum()
             (g,) = torch.autograd.grad(f, p)
-            f = float(f.item())
-            rec["loss"] = -f
+            rec["loss"] = -float(f.item())
+            binding.set_params(env, params)
+            fv = float((w_val * binding.logq(env, b_val, precision="f32")[0]).sum().item())
+            rec["val_loss"] = -fv
             if lr is None:
                 lr = step * float(params.norm()) / max(float(g.norm()), 1e-30)
             for _ in range(max_backtrack):
                 cand = params + lr * g
                 binding.set_params(env, cand)
-                fc = float((w * binding.logq(env, batch, precision="f32")[0]).sum().item())
-                if fc == fc and fc > -float("inf") and fc >= f:
+                fc = float((w_val * binding.logq(env, b_val, precision="f32")[0]).sum().item())
+                if fc == fc and fc > -float("inf") and fc >= fv:
                     params = cand
-                    rec.update(kept=True, loss_after=-fc)
+                    rec.update(kept=True, val_loss_after=-fc)
                     lr *= 1.25
                     break
                 lr *= 0.5
