@@ -250,6 +250,13 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
         const float fm = up ? fdiff : fsame;   // s = -1
         const float fp = up ? fsame : fdiff;   // s = +1
         uint64_t x = 0;
+        // couplings of the site's energy term, read while the UMMA runs
+        float e_h = 0.0f, e_jh = 0.0f, e_jv = 0.0f;
+        if (left && h == 0) {
+          e_h = h_row[c];
+          if (c > 0) e_jh = jh_row[c - 1];
+          if (r > 0) e_jv = jv_row[c];
+        }
         if (left) {
           if (c + 2 < Lx) {
             // R_{c+2} into L2 one step ahead: each lane fetches one of its warp's 32 lines
@@ -364,9 +371,9 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
               pexp -= 60;
             }
             flag |= bad ? TNMC_FLAG_NUMERIC : 0;
-            float loc = h_row[c];
-            if (c > 0) loc += jh_row[c - 1] * (s_left ? 1.0f : -1.0f);
-            if (r > 0) loc += jv_row[c] * (up ? 1.0f : -1.0f);
+            float loc = e_h;
+            if (c > 0) loc += e_jh * (s_left ? 1.0f : -1.0f);
+            if (r > 0) loc += e_jv * (up ? 1.0f : -1.0f);
             Erow -= (plus ? 1.0f : -1.0f) * loc;
             s_left = plus;
           }
