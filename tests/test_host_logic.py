@@ -1,0 +1,48 @@
+"""Host-side logic that needs no GPU: residence weights of the tuning loop and the
+reference arm's JSON line of bench.py."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+torch = pytest.importorskip("torch")
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_residence_weights_by_hand():
+    from paper_2104_13264_gb300.tuning import residence_weights
+    acc = torch.tensor([[0, 1, 0, 0, 1, 0],
+                        [0, 0, 0, 0, 0, 0],
+                        [1, 1, 1, 1, 1, 1],
+                        [1, 0, 0, 0, 0, 0]], dtype=torch.uint8)
+    w_acc, w_held = residence_weights(acc)
+    assert w_acc.tolist() == [[0, 3, 0, 0, 2, 0], [0] * 6, [1] * 6, [6, 0, 0, 0, 0, 0]]
+    assert w_held.tolist() == [1, 6, 0, 0]
+
+
+def test_residence_weights_sum_to_T():
+    from paper_2104_13264_gb300.tuning import residence_weights
+    g = torch.Generator().manual_seed(0)
+    acc = (torch.rand(50, 37, generator=g) < 0.3).to(torch.uint8)
+    w_acc, w_held = residence_weights(acc)
+    assert torch.equal(w_acc.sum(dim=1) + w_held, torch.full((50,), 37))
+    assert bool(((w_acc > 0) == acc.bool()).all())
+
+
+def test_reference_arm_prints_contract_line():
+    env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
+    p = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--config", "c1",
+                        "--steps", "1", "--warmup", "0", "--cpu-batch", "64"],
+                       capture_output=True, text=True, env=env, timeout=600, cwd=ROOT)
+    assert p.returncode == 0, p.stderr[-2000:]
+    line = json.loads(p.stdout.strip().splitlines()[-1])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["value"] > 0
+    assert line["config"]["workload"] == "c1"
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
