@@ -114,11 +114,11 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
   float4* sR = reinterpret_cast<float4*>(sB + kStageBytes);                  // [2][8][128] float4
   uint64_t* bars = reinterpret_cast<uint64_t*>(sB + kStageBytes + kRBytes);  // [0] tile, [1] UMMA, [2] R
   uint32_t* misc = reinterpret_cast<uint32_t*>(bars + 3);                    // [0] tmem base, [1] abort
-  float* xw = reinterpret_cast<float*>(misc + 4);                             // [2 halves][2][128] partial w
-  float* xm = xw + 4 * kTile;                                                  // [2 halves][128] partial max
+  float* xw = reinterpret_cast<float*>(misc + 4);   // [2 halves][4][128]: partial w(-), w(+), max|U(-)|, max|U(+)|
+  float* xm = xw;                                   // right steps: [2 halves][128] partial max
   const int Lx = a.e.Lx, Ly = a.e.Ly;
   const int W = (Lx + 31) >> 5;
-  uint32_t* bits_prev = reinterpret_cast<uint32_t*>(xm + 2 * kTile);
+  uint32_t* bits_prev = reinterpret_cast<uint32_t*>(xw + 8 * kTile);
   uint32_t* bits_cur = bits_prev + W * kTile;
 
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -331,7 +331,10 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
           }
           // partial dot products over this half, in four interleaved chains; R_{c+1} is
           // read from the shared buffer chunk by chunk (e_0 at the right end of the row)
+          // (and the maxima of |U(-)|, |U(+)| over this half, so that one exchange serves
+          // both the conditional and the rescaling of Lambda_{c+1})
           float a0[4] = {0.0f, 0.0f, 0.0f, 0.0f}, a1[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+          float n0 = 0.0f, n1 = 0.0f;
           const float4* src = sR + h * (8 * kTile) + t;
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
@@ -340,17 +343,20 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
             const float r4[4] = {q4.x, q4.y, q4.z, q4.w};
 #pragma unroll
             for (int z = 0; z < 4; ++z) {
-              a0[z] = fmaf(__uint_as_float(u0[4 * j + z]), r4[z], a0[z]);
-              a1[z] = fmaf(__uint_as_float(u1[4 * j + z]), r4[z], a1[z]);
+              const float x0 = __uint_as_float(u0[4 * j + z]), x1 = __uint_as_float(u1[4 * j + z]);
+              a0[z] = fmaf(x0, r4[z], a0[z]);
+              a1[z] = fmaf(x1, r4[z], a1[z]);
+              n0 = fmaxf(n0, fabsf(x0));
+              n1 = fmaxf(n1, fabsf(x1));
             }
           }
-          const float p0 = (a0[0] + a0[1]) + (a0[2] + a0[3]);
-          const float p1 = (a1[0] + a1[1]) + (a1[2] + a1[3]);
-          xw[(2 * h) * kTile + t] = p0;
-          xw[(2 * h + 1) * kTile + t] = p1;
+          xw[(4 * h) * kTile + t] = (a0[0] + a0[1]) + (a0[2] + a0[3]);
+          xw[(4 * h + 1) * kTile + t] = (a1[0] + a1[1]) + (a1[2] + a1[3]);
+          xw[(4 * h + 2) * kTile + t] = n0;
+          xw[(4 * h + 3) * kTile + t] = n1;
           pair_sync(warp);
-          float w0 = xw[t] + xw[2 * kTile + t];            // half 0 + half 1, same order in both
-          float w1 = xw[kTile + t] + xw[3 * kTile + t];
+          float w0 = xw[t] + xw[4 * kTile + t];            // half 0 + half 1, same order in both
+          float w1 = xw[kTile + t] + xw[5 * kTile + t];
           w0 = fmaxf(w0 * fm, 0.0f);
           w1 = fmaxf(w1 * fp, 0.0f);
           const float tot = w0 + w1;
@@ -377,18 +383,13 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
             Erow -= (plus ? 1.0f : -1.0f) * loc;
             s_left = plus;
           }
-          // Lambda_{c+1} = f(s) U[s], rescaled
+          // Lambda_{c+1} = f(s) U[s], rescaled; max |f(s) U[s]| = f(s) max |U[s]| (fs > 0,
+          // rounding is monotone), so the exchanged maxima give the scale directly
           const float fs = plus ? fp : fm;
-          float m4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+          const float mraw = plus ? fmaxf(xw[3 * kTile + t], xw[7 * kTile + t]) : fmaxf(xw[2 * kTile + t], xw[6 * kTile + t]);
+          const float mx = mraw * fs;
 #pragma unroll
-          for (int q = 0; q < 32; ++q) {
-            v[q] = __uint_as_float(plus ? u1[q] : u0[q]) * fs;
-            m4[q & 3] = fmaxf(m4[q & 3], fabsf(v[q]));
-          }
-          float mx = fmaxf(fmaxf(m4[0], m4[1]), fmaxf(m4[2], m4[3]));
-          xm[h * kTile + t] = mx;
-          pair_sync(warp);
-          mx = fmaxf(xm[t], xm[kTile + t]);
+          for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(plus ? u1[q] : u0[q]) * fs;
           const float sc = (mx > 0.0f && mx < INFINITY) ? pow2f(-ilogb_f(mx)) : 1.0f;
 #pragma unroll
           for (int q = 0; q < 32; ++q) v[q] *= sc;
@@ -514,7 +515,7 @@ tnmc_status tnmc_launch_sample_tc(const tnmc_env* env, int64_t B, uint64_t seed,
   }
   const int W = (d.Lx + 31) / 32;
   const size_t smem = 1024 + 2 * kVecBytes + kStageBytes + kRBytes + 3 * 8 + 16 +
-                      (size_t)6 * kTile * sizeof(float) + (size_t)2 * W * kTile * sizeof(uint32_t);
+                      (size_t)8 * kTile * sizeof(float) + (size_t)2 * W * kTile * sizeof(uint32_t);
   int dev = 0, nsm = 0, max_optin = 0;
   TNMC_CUDA_TRY(cudaGetDevice(&dev));
   TNMC_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
