@@ -40,7 +40,8 @@ constexpr uint32_t kTileBytes = kN * kK * 2;   // 16 KiB: one BF16 operand tile
 constexpr uint32_t kStageBytes = 2 * kTileBytes;   // hi + lo tiles of one (r, c)
 constexpr uint32_t kVecBytes = kTile * kK * 2;  // 16 KiB (one BF16 A operand)
 constexpr uint32_t kRBytes = kTile * kK * 4;    // 32 KiB: R_{c+1} of the tile, FP32
-constexpr uint32_t kPollLimit = 1u << 24;
+constexpr uint32_t kPollLimit = 1u << 16;    // polls of a bounded wait ...
+constexpr uint32_t kPollHintNs = 1u << 16;   // ... each parked up to ~65 us: at most ~4 s
 
 struct TcArgs {
   DeviceEnv e;
@@ -219,7 +220,7 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
                            umma::smem_u32(&bars[2]));
             ++r_issued;
           }
-          if (!umma::mbar_wait(umma::smem_u32(&bars[0]), (uint32_t)(g & 1), kPollLimit)) {
+          if (!umma::mbar_wait_parked(umma::smem_u32(&bars[0]), (uint32_t)(g & 1), kPollLimit, kPollHintNs)) {
             set_status(a.e.status, TNMC_E_TIMEOUT);
             misc[1] = 1;
           } else {
@@ -280,7 +281,7 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
             }
           }
         }
-        if (!umma::mbar_wait(umma::smem_u32(&bars[1]), (uint32_t)(g & 1), kPollLimit)) {
+        if (!umma::mbar_wait_parked(umma::smem_u32(&bars[1]), (uint32_t)(g & 1), kPollLimit, kPollHintNs)) {
           set_status(a.e.status, TNMC_E_TIMEOUT);
           misc[1] = 1;
         }
@@ -321,7 +322,7 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
         } else {
           // ---- left-sweep epilogue: w(s) = f(s) <U[s], R_{c+1}>, draw, Lambda_{c+1} ----
           if (rcopy) {
-            if (!umma::mbar_wait(umma::smem_u32(&bars[2]), nr & 1u, kPollLimit)) {
+            if (!umma::mbar_wait_parked(umma::smem_u32(&bars[2]), nr & 1u, kPollLimit, kPollHintNs)) {
               set_status(a.e.status, TNMC_E_TIMEOUT);
               misc[1] = 1;
             } else if (tid == 0) {
@@ -441,9 +442,9 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
   // teardown: let copies still in flight land (bounded), then free TMEM
   if (tid == 0) {
     for (int64_t q = g; q < issued; ++q)
-      (void)umma::mbar_wait(umma::smem_u32(&bars[0]), (uint32_t)(q & 1), kPollLimit);
+      (void)umma::mbar_wait_parked(umma::smem_u32(&bars[0]), (uint32_t)(q & 1), kPollLimit, kPollHintNs);
     for (uint32_t q = r_done; q < r_issued; ++q)
-      (void)umma::mbar_wait(umma::smem_u32(&bars[2]), q & 1u, kPollLimit);
+      (void)umma::mbar_wait_parked(umma::smem_u32(&bars[2]), q & 1u, kPollLimit, kPollHintNs);
     bulk_wait_all();
   }
   umma::fence_before_sync();

@@ -102,6 +102,23 @@ __device__ inline bool mbar_wait(uint32_t mbar, uint32_t parity, uint32_t limit)
   return false;
 }
 
+// Bounded wait that lets the hardware park the thread between polls: each try_wait may
+// suspend for up to `hint_ns` nanoseconds and returns as soon as the phase completes, so
+// a waiting warp issues a handful of instructions instead of spinning.  Returns false
+// after `limit` polls (at most limit * hint_ns of waiting).
+__device__ inline bool mbar_wait_parked(uint32_t mbar, uint32_t parity, uint32_t limit, uint32_t hint_ns) {
+  for (uint32_t i = 0; i < limit; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity), "r"(hint_ns)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
 // One bulk copy global -> shared (16-byte aligned, size a multiple of 16), completing on mbar.
 __device__ inline void bulk_g2s(uint32_t dst_smem, const void* src, uint32_t bytes, uint32_t mbar) {
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
