@@ -119,7 +119,8 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
   float* xm = xw;                                   // right steps: [2 halves][128] partial max
   const int Lx = a.e.Lx, Ly = a.e.Ly;
   const int W = (Lx + 31) >> 5;
-  uint32_t* bits_prev = reinterpret_cast<uint32_t*>(xw + 8 * kTile);
+  uint32_t* xs = reinterpret_cast<uint32_t*>(xw + 8 * kTile);   // [2][128]: the site's 64-bit uniform
+  uint32_t* bits_prev = xs + 2 * kTile;
   uint32_t* bits_cur = bits_prev + W * kTile;
 
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -266,7 +267,7 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
                                (size_t)(lane >> 2) * kTile + 8 * (lane & 3);
             asm volatile("prefetch.global.L2 [%0];" ::"l"(pf));
           }
-          if (!a.spins_in) {
+          if (!a.spins_in && h == 0) {   // half 0 draws the word, half 1 receives it with the dots
             const int64_t site = (int64_t)r * Lx + c;
             if ((site & 1) && (site >> 1) == pair_id) {
               x = pair_word;
@@ -355,7 +356,12 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
           xw[(4 * h + 1) * kTile + t] = (a1[0] + a1[1]) + (a1[2] + a1[3]);
           xw[(4 * h + 2) * kTile + t] = n0;
           xw[(4 * h + 3) * kTile + t] = n1;
+          if (h == 0) {
+            xs[t] = (uint32_t)x;
+            xs[kTile + t] = (uint32_t)(x >> 32);
+          }
           pair_sync(warp);
+          if (h == 1) x = (uint64_t)xs[t] | ((uint64_t)xs[kTile + t] << 32);
           float w0 = xw[t] + xw[4 * kTile + t];            // half 0 + half 1, same order in both
           float w1 = xw[kTile + t] + xw[5 * kTile + t];
           w0 = fmaxf(w0 * fm, 0.0f);
@@ -516,7 +522,7 @@ tnmc_status tnmc_launch_sample_tc(const tnmc_env* env, int64_t B, uint64_t seed,
   }
   const int W = (d.Lx + 31) / 32;
   const size_t smem = 1024 + 2 * kVecBytes + kStageBytes + kRBytes + 3 * 8 + 16 +
-                      (size_t)8 * kTile * sizeof(float) + (size_t)2 * W * kTile * sizeof(uint32_t);
+                      (size_t)10 * kTile * sizeof(float) + (size_t)2 * W * kTile * sizeof(uint32_t);
   int dev = 0, nsm = 0, max_optin = 0;
   TNMC_CUDA_TRY(cudaGetDevice(&dev));
   TNMC_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
