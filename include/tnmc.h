@@ -33,6 +33,7 @@
 #ifndef TNMC_H
 #define TNMC_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -90,6 +91,24 @@ typedef struct {
   int64_t smem_bytes;      /* dynamic shared memory per CTA                       */
   int64_t scratch_bytes;   /* device bytes of the per-CTA right-vector stacks     */
 } tnmc_batch_info_t;
+
+/*
+ * Device-memory hook.  Every device allocation the library makes (environment
+ * arenas, sampler and gradient scratch, builder work space, batch plans, the MH
+ * scan's temporary) goes through alloc_fn / free_fn, so that a caller's allocator
+ * (for instance PyTorch's caching allocator) can own the memory.  alloc_fn returns
+ * a device pointer of at least `bytes` bytes, usable in stream order on `stream`
+ * (a cudaStream_t, possibly NULL), or NULL on failure; free_fn releases a pointer
+ * it returned (`stream` is the stream of the last use, or NULL once the device has
+ * been synchronised).  Objects keep the hook that was current when they were
+ * created and free through it.  Passing NULL, NULL restores the default
+ * (cudaMallocAsync / cudaFreeAsync).  Set it before creating objects, from one
+ * thread; it applies process-wide.  The paper has no counterpart: this is plumbing
+ * for callers that manage device memory themselves.
+ */
+typedef void* (*tnmc_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*tnmc_free_fn)(void* ptr, size_t bytes, void* stream, void* ctx);
+tnmc_status tnmc_set_allocator(tnmc_alloc_fn alloc_fn, tnmc_free_fn free_fn, void* ctx);
 
 /* Thread-local text of the last error (empty string if none). */
 const char* tnmc_last_error(void);

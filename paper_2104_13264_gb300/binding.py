@@ -73,7 +73,12 @@ SIGNATURES = {
     "tnmc_logq_batched": ([_P, _P, _P, _P, _P, _P], _INT),
     "tnmc_batch_init_chains": ([_P, _U64, _P, _P, _P, _P], _INT),
     "tnmc_mh_batched": ([_P, _P, _P, _P, _P, _P, _P, _P, _P, _P], _INT),
+    "tnmc_set_allocator": ([_P, _P, _P], _INT),
 }
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_hooks = None   # keeps the ctypes callbacks alive while the library may call them
 
 
 def lib():
@@ -89,6 +94,32 @@ def lib():
             f.restype = res
         _lib = L
     return _lib
+
+
+def use_torch_allocator():
+    """Route the library's device allocations through PyTorch's caching allocator
+    (tnmc_set_allocator).  Objects created afterwards allocate and free through it."""
+    import torch
+    global _hooks
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(), stream or 0)
+        except Exception:  # noqa: BLE001 -- out of memory: the library reports TNMC_E_NOMEM
+            return None
+
+    def _free(ptr, nbytes, stream, ctx):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    hooks = (ALLOC_FN(_alloc), FREE_FN(_free))
+    _check(lib().tnmc_set_allocator(ctypes.cast(hooks[0], _P), ctypes.cast(hooks[1], _P), None))
+    _hooks = hooks
+
+
+def use_default_allocator():
+    """Back to cudaMallocAsync / cudaFreeAsync for objects created afterwards.  Objects
+    created under the torch hook keep freeing through it, so its callbacks stay referenced."""
+    _check(lib().tnmc_set_allocator(None, None, None))
 
 
 def _check(status):

@@ -20,6 +20,49 @@ void tnmc_set_error(const char* fmt, ...) {
   va_end(ap);
 }
 
+namespace tnmc {
+
+static Allocator g_alloc;   // process-wide hook (tnmc_set_allocator)
+
+Allocator current_allocator() { return g_alloc; }
+
+void* dev_alloc(const Allocator& A, size_t bytes, cudaStream_t s) {
+  if (bytes == 0) bytes = 1;
+  if (A.alloc) return A.alloc(bytes, s, A.ctx);
+  void* p = nullptr;
+  if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+void dev_free(const Allocator& A, void* p, size_t bytes, cudaStream_t s) {
+  if (!p) return;
+  if (A.free) {
+    A.free(p, bytes, s, A.ctx);
+    return;
+  }
+  if (cudaFreeAsync(p, s) != cudaSuccess) (void)cudaGetLastError();
+}
+
+tnmc_status grow_scratch(tnmc_env* env, size_t need, cudaStream_t s, const char* what) {
+  if (env->scratch.bytes >= need) return TNMC_OK;
+  dev_free(env->alloc, env->scratch.ptr, env->scratch.bytes, s);
+  env->scratch.ptr = nullptr;
+  env->scratch.bytes = 0;
+  void* p = dev_alloc(env->alloc, need, s);
+  if (!p) {
+    tnmc_set_error("cannot allocate %zu bytes of %s scratch", need, what);
+    return TNMC_E_NOMEM;
+  }
+  env->scratch.ptr = p;
+  env->scratch.bytes = need;
+  return TNMC_OK;
+}
+
+}  // namespace tnmc
+
 #define CHECK_ARG(cond, ...)          \
   do {                                \
     if (!(cond)) {                    \
@@ -97,9 +140,9 @@ tnmc_status env_create(const tnmc_lattice* lat, double beta, int chi, int precis
     tnmc_set_error("host allocation failed");
     return TNMC_E_NOMEM;
   }
-  char* base = nullptr;
-  if (cudaMalloc(&base, total) != cudaSuccess) {
-    (void)cudaGetLastError();
+  env->alloc = current_allocator();
+  char* base = static_cast<char*>(dev_alloc(env->alloc, total, s));
+  if (!base) {
     delete env;
     tnmc_set_error("cannot allocate %zu bytes for the environment", total);
     return TNMC_E_NOMEM;
@@ -156,7 +199,7 @@ tnmc_status env_create(const tnmc_lattice* lat, double beta, int chi, int precis
   if (st != TNMC_OK) {
     if (!g_err[0]) tnmc_set_error("CUDA error while uploading the couplings: %s", cudaGetErrorString(cudaGetLastError()));
     (void)cudaStreamSynchronize(s);
-    cudaFree(base);
+    dev_free(env->alloc, base, total, s);
     delete env;
     return st;
   }
@@ -167,8 +210,9 @@ tnmc_status env_create(const tnmc_lattice* lat, double beta, int chi, int precis
 void env_destroy(tnmc_env* env, cudaStream_t s) {
   if (!env) return;
   (void)cudaStreamSynchronize(s);
-  if (env->scratch.ptr) cudaFree(env->scratch.ptr);
-  cudaFree(env->arena);
+  dev_free(env->alloc, env->scratch.ptr, env->scratch.bytes, s);
+  dev_free(env->alloc, env->arena, env->arena_bytes, s);
+  (void)cudaStreamSynchronize(s);
   delete env;
 }
 
@@ -199,9 +243,8 @@ tnmc_status tnmc_build_env(const tnmc_lattice* lat, double beta, int chi, int pr
   void* work = nullptr;
   const size_t wbytes = tnmc_build_work_bytes(d.Lx, d.Ly, d.P);
   do {
-    if (cudaMallocAsync(&work, wbytes, s) != cudaSuccess) {
-      (void)cudaGetLastError();
-      work = nullptr;
+    work = dev_alloc(env->alloc, wbytes, s);
+    if (!work) {
       st = TNMC_E_NOMEM;
       tnmc_set_error("cannot allocate %zu bytes of builder scratch", wbytes);
       break;
@@ -210,7 +253,7 @@ tnmc_status tnmc_build_env(const tnmc_lattice* lat, double beta, int chi, int pr
     if (st != TNMC_OK) break;
     st = env_derive(env, s);
   } while (0);
-  if (work) (void)cudaFreeAsync(work, s);
+  dev_free(env->alloc, work, wbytes, s);
   if (st != TNMC_OK) {
     if (st == TNMC_E_CUDA && !g_err[0]) tnmc_set_error("CUDA error while building: %s", cudaGetErrorString(cudaGetLastError()));
     env_destroy(env, s);
@@ -245,13 +288,14 @@ tnmc_status tnmc_build_env_batched(int n, const tnmc_lattice* lats, const double
     woff[i] = wtotal;
     wtotal += align256(tnmc_build_work_bytes(d.Lx, d.Ly, d.P));
   }
+  const Allocator A = current_allocator();
   void* work = nullptr;
   void* args = nullptr;
   if (st == TNMC_OK) {
     do {
-      if (cudaMallocAsync(&work, wtotal, s) != cudaSuccess ||
-          cudaMallocAsync(&args, (size_t)n * tnmc_build_args_bytes(), s) != cudaSuccess) {
-        (void)cudaGetLastError();
+      work = dev_alloc(A, wtotal, s);
+      args = work ? dev_alloc(A, (size_t)n * tnmc_build_args_bytes(), s) : nullptr;
+      if (!work || !args) {
         st = TNMC_E_NOMEM;
         tnmc_set_error("cannot allocate %zu bytes of builder scratch", wtotal);
         break;
@@ -260,8 +304,8 @@ tnmc_status tnmc_build_env_batched(int n, const tnmc_lattice* lats, const double
       for (int i = 0; i < n && st == TNMC_OK; ++i) st = env_derive(envs[i], s);
     } while (0);
   }
-  if (work) (void)cudaFreeAsync(work, s);
-  if (args) (void)cudaFreeAsync(args, s);
+  dev_free(A, work, wtotal, s);
+  dev_free(A, args, (size_t)n * tnmc_build_args_bytes(), s);
   if (st != TNMC_OK) {
     if (st == TNMC_E_CUDA && !g_err[0]) tnmc_set_error("CUDA error while building: %s", cudaGetErrorString(cudaGetLastError()));
     for (int i = 0; i < n; ++i) env_destroy(envs[i], s);
@@ -274,9 +318,19 @@ tnmc_status tnmc_build_env_batched(int n, const tnmc_lattice* lats, const double
 tnmc_status tnmc_env_free(tnmc_env* env) {
   if (!env) return TNMC_OK;
   cudaDeviceSynchronize();
-  if (env->scratch.ptr) cudaFree(env->scratch.ptr);
-  if (env->arena) cudaFree(env->arena);
+  dev_free(env->alloc, env->scratch.ptr, env->scratch.bytes, nullptr);
+  dev_free(env->alloc, env->arena, env->arena_bytes, nullptr);
+  cudaDeviceSynchronize();
   delete env;
+  return TNMC_OK;
+}
+
+tnmc_status tnmc_set_allocator(tnmc_alloc_fn alloc_fn, tnmc_free_fn free_fn, void* ctx) {
+  g_err[0] = 0;
+  CHECK_ARG((alloc_fn == nullptr) == (free_fn == nullptr), "alloc_fn and free_fn must both be set or both be NULL");
+  tnmc::g_alloc.alloc = alloc_fn;
+  tnmc::g_alloc.free = free_fn;
+  tnmc::g_alloc.ctx = alloc_fn ? ctx : nullptr;
   return TNMC_OK;
 }
 

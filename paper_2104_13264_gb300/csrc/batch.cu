@@ -179,7 +179,8 @@ struct tnmc_batch {
   int64_t prop_rows = 0, prop_bytes = 0, chain_rows = 0, chain_bytes = 0;
   int64_t items_prop = 0, items_chain = 0;
   int grid = 0;
-  size_t smem = 0, stack_elems = 0, scratch_bytes = 0;
+  size_t smem = 0, stack_elems = 0, scratch_bytes = 0, arena_bytes = 0;
+  tnmc::Allocator alloc;   // the hook current when the plan was created
   // device memory: one arena for the tables, one for the per-CTA stacks
   void* arena = nullptr;
   void* scratch = nullptr;
@@ -301,8 +302,9 @@ tnmc_status dispatch_batched(tnmc_batch* p, bool chains, const int8_t* spins_in,
 void free_plan(tnmc_batch* p) {
   if (!p) return;
   cudaDeviceSynchronize();
-  if (p->scratch) cudaFree(p->scratch);
-  if (p->arena) cudaFree(p->arena);
+  tnmc::dev_free(p->alloc, p->scratch, p->scratch_bytes, nullptr);
+  tnmc::dev_free(p->alloc, p->arena, p->arena_bytes, nullptr);
+  cudaDeviceSynchronize();
   delete p;
 }
 
@@ -409,16 +411,20 @@ tnmc_status tnmc_batch_create(int n, tnmc_env* const* envs, const int64_t* B, in
   const size_t o_ip = take(ip.size() * sizeof(int2)), o_ic = take(ic.size() * sizeof(int2));
   const size_t o_mh = take(n * sizeof(tnmc::MhInst)), o_cnt = take(2 * sizeof(unsigned int));
   const size_t o_par = take(2 * sizeof(uint64_t)), o_last = take((size_t)p->chain_rows * 8);
-  char* base = nullptr;
-  if (cudaMalloc(&base, off) != cudaSuccess || cudaMalloc(&p->scratch, p->scratch_bytes) != cudaSuccess) {
-    (void)cudaGetLastError();
-    if (base) cudaFree(base);
-    p->scratch = nullptr;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  p->alloc = current_allocator();
+  char* base = static_cast<char*>(dev_alloc(p->alloc, off, s));
+  p->scratch = base ? dev_alloc(p->alloc, p->scratch_bytes, s) : nullptr;
+  if (!base || !p->scratch) {
+    const size_t sb = p->scratch_bytes;
+    dev_free(p->alloc, base, off, s);
+    (void)cudaStreamSynchronize(s);
     delete p;
-    tnmc_set_error("cannot allocate the batch plan (%zu + %zu bytes)", off, p->scratch_bytes);
+    tnmc_set_error("cannot allocate the batch plan (%zu + %zu bytes)", off, sb);
     return TNMC_E_NOMEM;
   }
   p->arena = base;
+  p->arena_bytes = off;
   p->tab_prop = base + o_tp;
   p->tab_chain = base + o_tc;
   p->d_prop_row = reinterpret_cast<int64_t*>(base + o_pr);
@@ -447,7 +453,6 @@ tnmc_status tnmc_batch_create(int n, tnmc_env* const* envs, const int64_t* B, in
     memcpy(tp.data(), a.data(), tab_bytes);
     memcpy(tc.data(), b.data(), tab_bytes);
   }
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaMemsetAsync(base, 0, off, s);
   auto up = [&](void* dst, const void* src, size_t bytes) {
     if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s);

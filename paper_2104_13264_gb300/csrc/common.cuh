@@ -49,6 +49,17 @@ struct Scratch {
   size_t bytes = 0;
 };
 
+// The device-memory hook an object allocates and frees through (tnmc_set_allocator).
+struct Allocator {
+  tnmc_alloc_fn alloc = nullptr;   // nullptr: cudaMallocAsync / cudaFreeAsync
+  tnmc_free_fn free = nullptr;
+  void* ctx = nullptr;
+};
+
+Allocator current_allocator();
+void* dev_alloc(const Allocator& A, size_t bytes, cudaStream_t s);   // nullptr on failure
+void dev_free(const Allocator& A, void* p, size_t bytes, cudaStream_t s);
+
 }  // namespace tnmc
 
 struct tnmc_env {
@@ -67,7 +78,13 @@ struct tnmc_env {
   float* Jh32 = nullptr;
   float* Jv32 = nullptr;
   tnmc::Scratch scratch;         // sampler scratch (grown on demand)
+  tnmc::Allocator alloc;         // the hook current when the env was created
 };
+
+namespace tnmc {
+// Grow env->scratch to at least `need` bytes (the old block is released in stream order).
+tnmc_status grow_scratch(tnmc_env* env, size_t need, cudaStream_t s, const char* what);
+}  // namespace tnmc
 
 namespace tnmc {
 

@@ -262,18 +262,9 @@ tnmc_status tnmc_launch_logq_grad(const tnmc_env* env, int64_t B, const int8_t* 
   const size_t per_cta = (size_t)3 * (d.Lx + 1) * d.P * kNT + (size_t)4 * d.Lx * kNT;
   const size_t need = (size_t)ntiles * per_cta * sizeof(float);
   tnmc_env* me = const_cast<tnmc_env*>(env);
-  if (me->scratch.bytes < need) {
-    if (me->scratch.ptr) TNMC_CUDA_TRY(cudaFreeAsync(me->scratch.ptr, stream));
-    me->scratch.ptr = nullptr;
-    me->scratch.bytes = 0;
-    void* p = nullptr;
-    if (cudaMallocAsync(&p, need, stream) != cudaSuccess) {
-      (void)cudaGetLastError();
-      tnmc_set_error("cannot allocate %zu bytes of gradient scratch", need);
-      return TNMC_E_NOMEM;
-    }
-    me->scratch.ptr = p;
-    me->scratch.bytes = need;
+  {
+    const tnmc_status gs = grow_scratch(me, need, stream, "gradient");
+    if (gs != TNMC_OK) return gs;
   }
   GradArgs a;
   a.e = d;

@@ -81,8 +81,11 @@ tnmc_status tnmc_launch_mh(const tnmc_env* env, int64_t C, int64_t T, const int8
   using namespace tnmc;
   if (C == 0 || T == 0) return TNMC_OK;
   const int64_t n = (int64_t)env->d.Lx * env->d.Ly;
-  int64_t* last = nullptr;
-  TNMC_CUDA_TRY(cudaMallocAsync(&last, C * sizeof(int64_t), stream));
+  int64_t* last = static_cast<int64_t*>(dev_alloc(env->alloc, C * sizeof(int64_t), stream));
+  if (!last) {
+    tnmc_set_error("cannot allocate %zu bytes for the MH scan", (size_t)C * sizeof(int64_t));
+    return TNMC_E_NOMEM;
+  }
   const int threads = 128;
   const int64_t blocks = (C + threads - 1) / threads;
   mh_scan_kernel<<<(unsigned)blocks, threads, 0, stream>>>(C, T, env->d.beta, prop_logq, prop_energy, chain_logq,
@@ -92,7 +95,7 @@ tnmc_status tnmc_launch_mh(const tnmc_env* env, int64_t C, int64_t T, const int8
   const int64_t cb = C < 65535 ? C : 65535;
   mh_copy_kernel<<<(unsigned)cb, 256, 0, stream>>>(C, n, last, prop_spins, chain_spins);
   TNMC_CUDA_TRY(cudaGetLastError());
-  TNMC_CUDA_TRY(cudaFreeAsync(last, stream));
+  dev_free(env->alloc, last, C * sizeof(int64_t), stream);
   return TNMC_OK;
 }
 

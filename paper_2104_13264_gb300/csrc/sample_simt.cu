@@ -83,18 +83,9 @@ tnmc_status launch_sample_t(const tnmc_env* env, const T* L, const T* R, const T
   if (grid < 1) grid = 1;
   const size_t need = (size_t)grid * (d.Lx + 1) * d.P * NT * sizeof(T);
   tnmc_env* me = const_cast<tnmc_env*>(env);
-  if (me->scratch.bytes < need) {
-    if (me->scratch.ptr) TNMC_CUDA_TRY(cudaFreeAsync(me->scratch.ptr, stream));
-    me->scratch.ptr = nullptr;
-    me->scratch.bytes = 0;
-    void* p = nullptr;
-    if (cudaMallocAsync(&p, need, stream) != cudaSuccess) {
-      (void)cudaGetLastError();
-      tnmc_set_error("cannot allocate %zu bytes of sampler scratch", need);
-      return TNMC_E_NOMEM;
-    }
-    me->scratch.ptr = p;
-    me->scratch.bytes = need;
+  {
+    const tnmc_status gs = grow_scratch(me, need, stream, "sampler");
+    if (gs != TNMC_OK) return gs;
   }
   SampleArgs<T> a;
   a.e = d;

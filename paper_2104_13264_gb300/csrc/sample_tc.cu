@@ -555,18 +555,9 @@ tnmc_status tnmc_launch_sample_tc(const tnmc_env* env, int64_t B, uint64_t seed,
   if (grid > ntiles) grid = ntiles;
   const size_t need = (size_t)grid * d.Lx * kTile * kK * sizeof(float);
   tnmc_env* me = const_cast<tnmc_env*>(env);
-  if (me->scratch.bytes < need) {
-    if (me->scratch.ptr) TNMC_CUDA_TRY(cudaFreeAsync(me->scratch.ptr, stream));
-    me->scratch.ptr = nullptr;
-    me->scratch.bytes = 0;
-    void* p = nullptr;
-    if (cudaMallocAsync(&p, need, stream) != cudaSuccess) {
-      (void)cudaGetLastError();
-      tnmc_set_error("cannot allocate %zu bytes of sampler scratch", need);
-      return TNMC_E_NOMEM;
-    }
-    me->scratch.ptr = p;
-    me->scratch.bytes = need;
+  {
+    const tnmc_status gs = grow_scratch(me, need, stream, "sampler");
+    if (gs != TNMC_OK) return gs;
   }
   TcArgs a;
   a.e = d;
