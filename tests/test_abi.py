@@ -63,3 +63,23 @@ def test_argument_errors_reported_without_gpu(libpath):
     lat2 = binding._Lattice(2, 2, J.ctypes.data, J.ctypes.data, hb.ctypes.data)
     assert L.tnmc_build_env(ctypes.byref(lat2), 1.0, 4, 0, None, ctypes.byref(out)) == 1
     assert b"not finite" in L.tnmc_last_error()
+
+
+def test_allocator_and_batch_argument_errors_without_gpu(libpath):
+    """tnmc_set_allocator wants both functions or neither; the batch calls check their
+    arguments before touching the device."""
+    from paper_2104_13264_gb300 import binding
+    L = binding.lib()
+
+    @binding.ALLOC_FN
+    def _alloc(n, s, ctx):
+        return None
+
+    assert L.tnmc_set_allocator(ctypes.cast(_alloc, ctypes.c_void_p), None, None) == 1
+    assert b"both" in L.tnmc_last_error()
+    assert L.tnmc_set_allocator(None, None, None) == 0
+    out = ctypes.c_void_p()
+    assert L.tnmc_batch_create(0, None, None, 1, 1, 128, 1, None, ctypes.byref(out)) == 1
+    assert L.tnmc_build_env_batched(-1, None, None, None, 0, None, None) == 1
+    assert L.tnmc_sample_batched(None, None, None, None, None, None) == 1
+    assert L.tnmc_mh_batched(None, None, None, None, None, None, None, None, None, None) == 1
