@@ -162,3 +162,29 @@ def independence_acceptance(pi, q):
 def tv_distance(pi, q):
     """||pi - q||_TV = 1/2 sum |pi - q| (eq. tv)."""
     return 0.5 * float(np.abs(np.asarray(pi) - np.asarray(q)).sum())
+
+
+def row_weight_vector(Jh, Jv, h, beta, r):
+    """psi_r(sigma_r): the exact weight of row r's configurations, by enumeration.
+
+    The Boltzmann weight of rows r..Ly-1 (their fields, horizontal bonds and the
+    vertical bonds among them) summed over rows r+1..Ly-1 -- the quantity the
+    boundary-MPS environment of row r stands for (App. A, eq. braket-top-tm-bot,
+    read bottom-up), without the vertical bonds to row r-1.  Entry j holds the
+    row configuration with s_c = +1 iff bit c of j.  Cost 2^(Lx (Ly - r)).
+    """
+    h = np.asarray(h, dtype=np.float64)
+    Ly, Lx = h.shape
+    Jh = np.asarray(Jh, dtype=np.float64).reshape(Ly, max(Lx - 1, 0))
+    Jv = np.asarray(Jv, dtype=np.float64).reshape(max(Ly - 1, 0), Lx)
+    _, logZ, pi, _ = boltzmann(Jh[r:], Jv[r:], h[r:], beta)
+    # boltzmann() enumerates the sub-lattice of rows r.. with row r in the low Lx bits
+    w = pi.reshape(-1, 1 << Lx).sum(axis=0)          # sum over the rows below
+    return w * math.exp(logZ)
+
+
+def schmidt_values(psi, Lx, c):
+    """Singular values of psi reshaped to (sites c..Lx-1) x (sites 0..c-1), divided by
+    their 2-norm: the Schmidt coefficients of the cut between sites c-1 and c."""
+    S = np.linalg.svd(np.asarray(psi).reshape(1 << (Lx - c), 1 << c), compute_uv=False)
+    return S / math.sqrt(float(np.sum(S * S)))

@@ -323,18 +323,21 @@ __device__ inline void tournament(int t, int i, int N, int& p, int& q) {
 // rotated while |gamma| > tol sqrt(alpha beta), tol = 1e-13 (above the rounding
 // level of a dot product of length <= 128).  Rows whose norm is below 1e-13 of
 // the largest are at the rounding level of the matrix: they carry no information
-// and are left out of the rotations (callers treat them as zero rows).
+// and are left out of the rotations (callers treat them as zero rows).  Returns
+// false when the last of kJacobiSweeps sweeps still rotated (not converged); the
+// value is the same on every thread.
 constexpr double kJacobiTol = 1e-13;
+constexpr int kJacobiSweeps = 40;
 constexpr double kNullRel = 1e-13;
 
-__device__ void jacobi_rows(double* J, int m, int n, int ld, double* d, int* flag) {
+__device__ bool jacobi_rows(double* J, int m, int n, int ld, double* d, int* flag) {
   const int N = m + (m & 1);
   const int npairs = N / 2;
   // blockDim.x / 64 lanes per pair (a power of two): all m/2 <= 64 pairs of a round
   // at once; the per-pair scalar work is repeated on every lane of a group
   const int L = blockDim.x / 64;
   const int grp = threadIdx.x / L, gl = threadIdx.x % L;
-  for (int sweep = 0; sweep < 40; ++sweep) {
+  for (int sweep = 0; sweep < kJacobiSweeps; ++sweep) {
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
       double s = 0.0;
       for (int x = 0; x < n; ++x) s += J[(size_t)i * ld + x] * J[(size_t)i * ld + x];
@@ -394,8 +397,9 @@ __device__ void jacobi_rows(double* J, int m, int n, int ld, double* d, int* fla
     }
     const int rotated = flag[0];
     __syncthreads();
-    if (!rotated) break;
+    if (!rotated) return true;
   }
+  return false;
 }
 
 // ---------------------------------------------------------------------------
@@ -421,7 +425,7 @@ __device__ double svd_sweep(const BuildArgs& a, Shared& sh, int r) {
     }
     for (int idx = threadIdx.x; idx < m * n; idx += blockDim.x) J[(idx / n) * ld + idx % n] = A[idx];
     __syncthreads();
-    jacobi_rows(J, m, n, ld, nrm, sh.flag);
+    if (!jacobi_rows(J, m, n, ld, nrm, sh.flag) && threadIdx.x == 0) set_status(a.status, TNMC_E_NUMERIC);
     for (int i = w; i < m; i += kWarps) {
       double s = 0.0;
       for (int x = lane; x < n; x += 32) s += J[i * ld + x] * J[i * ld + x];
@@ -780,7 +784,7 @@ __device__ inline int z2_col(int s, int j, int Dr, int er) {
 // with the rounds, tolerances and arithmetic of jacobi_rows (blockDim.x / 64 lanes per
 // pair, a power of two).  Sweeps continue until neither
 // sector rotates; a converged sector's extra sweep rotates nothing.
-__device__ void jacobi_rows2(double* J0, int m0, double* J1, int m1, int n, int ld, double* d0, double* d1,
+__device__ bool jacobi_rows2(double* J0, int m0, double* J1, int m1, int n, int ld, double* d0, double* d1,
                              int* flag) {
   const int half = blockDim.x >> 1;          // threads per sector
   const int sec = threadIdx.x >= half;
@@ -793,7 +797,7 @@ __device__ void jacobi_rows2(double* J0, int m0, double* J1, int m1, int n, int 
   const int Nmax = max(m0 + (m0 & 1), m1 + (m1 & 1));
   const int L = half / 32;                   // lanes per pair: all 32 pairs of a round at once
   const int grp = lt / L, gl = lt % L;
-  for (int sweep = 0; sweep < 40; ++sweep) {
+  for (int sweep = 0; sweep < kJacobiSweeps; ++sweep) {
     for (int i = lt; i < m; i += half) {
       double s = 0.0;
       for (int x = 0; x < n; ++x) s += J[(size_t)i * ld + x] * J[(size_t)i * ld + x];
@@ -851,8 +855,9 @@ __device__ void jacobi_rows2(double* J0, int m0, double* J1, int m1, int n, int 
     }
     const int rotated = flag[0] | flag[2];
     __syncthreads();
-    if (!rotated) break;
+    if (!rotated) return true;
   }
+  return false;
 }
 
 __device__ double svd_sweep_z2(const BuildArgs& a, ShZ2& sh, int r) {
@@ -880,12 +885,14 @@ __device__ double svd_sweep_z2(const BuildArgs& a, ShZ2& sh, int r) {
       J[l * ld + j] = A[(size_t)l * 2 * Dr + col];
     }
     __syncthreads();
+    bool converged = true;
     if (el <= 64 && Dl - el <= 64) {
-      jacobi_rows2(J, el, J + (size_t)el * ld, Dl - el, n, ld, nrm, nrm + el, sh.flag);
+      converged = jacobi_rows2(J, el, J + (size_t)el * ld, Dl - el, n, ld, nrm, nrm + el, sh.flag);
     } else {
-      if (el > 0) jacobi_rows(J, el, n, ld, nrm, sh.flag);
-      if (Dl - el > 0) jacobi_rows(J + (size_t)el * ld, Dl - el, n, ld, nrm + el, sh.flag);
+      if (el > 0) converged = jacobi_rows(J, el, n, ld, nrm, sh.flag);
+      if (Dl - el > 0) converged = jacobi_rows(J + (size_t)el * ld, Dl - el, n, ld, nrm + el, sh.flag) && converged;
     }
+    if (!converged && threadIdx.x == 0) set_status(a.status, TNMC_E_NUMERIC);
     for (int i = w; i < Dl; i += kWarps) {
       double sq = 0.0;
       for (int x = lane; x < n; x += 32) sq += J[i * ld + x] * J[i * ld + x];

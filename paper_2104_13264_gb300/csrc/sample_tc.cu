@@ -25,6 +25,7 @@
 // environment tile of the next step is copied as soon as the UMMA has read the current
 // one, while the epilogue runs.  Steps per row: (Lx - 1) right + Lx left.
 #include <math.h>
+#include <stdlib.h>
 
 #include "common.cuh"
 #include "umma.cuh"
@@ -59,6 +60,11 @@ struct TcArgs {
   double* energy;
   int32_t* flags;
   float4* stack;             // per CTA: [Lx][2 halves][8 chunks][128 samples] float4
+  const double* h64;         // FP64 couplings: the energy of non-integer instances
+  const double* Jh64;
+  const double* Jv64;
+  uint32_t poll_limit;       // polls of each wait inside the sampling loop (kPollLimit;
+                             // 0 makes every such wait give up at once)
 };
 
 __device__ inline float pow2f(int e) { return __int_as_float((e + 127) << 23); }   // 2^e, |e| < 127
@@ -141,6 +147,7 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
     for (int s = 0; s < 3; ++s) umma::mbar_init(umma::smem_u32(&bars[s]), s == 1 ? 2 : 1);
     umma::fence_mbar_init();
     misc[1] = 0;
+    misc[2] = 1;
   }
   umma::fence_before_sync();
   __syncthreads();
@@ -202,7 +209,7 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
       }
       float prod = 1.0f;
       int pexp = 0;
-      float Erow = 0.0f;
+      float Erow = 0.0f;      // integer couplings: exact in FP32 (others: FP64 at the row end)
       int s_left = 0;
       umma::fence_proxy_async();
       umma::fence_before_sync();
@@ -221,7 +228,10 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
                            umma::smem_u32(&bars[2]));
             ++r_issued;
           }
-          if (!umma::mbar_wait_parked(umma::smem_u32(&bars[0]), (uint32_t)(g & 1), kPollLimit, kPollHintNs)) {
+          const bool tile_ok = umma::mbar_wait_parked(umma::smem_u32(&bars[0]), (uint32_t)(g & 1), a.poll_limit,
+                                                      kPollHintNs);
+          misc[2] = tile_ok;
+          if (!tile_ok) {
             set_status(a.e.status, TNMC_E_TIMEOUT);
             misc[1] = 1;
           } else {
@@ -252,9 +262,10 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
         const float fm = up ? fdiff : fsame;   // s = -1
         const float fp = up ? fsame : fdiff;   // s = +1
         uint64_t x = 0;
-        // couplings of the site's energy term, read while the UMMA runs
+        // couplings of the site's energy term, read while the UMMA runs (FP32: exact for
+        // integer couplings; other couplings are read in FP64 where the term is added)
         float e_h = 0.0f, e_jh = 0.0f, e_jv = 0.0f;
-        if (left && h == 0) {
+        if (left && h == 0 && a.e.integer_couplings) {
           e_h = h_row[c];
           if (c > 0) e_jh = jh_row[c - 1];
           if (r > 0) e_jv = jv_row[c];
@@ -282,13 +293,15 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
             }
           }
         }
-        if (!umma::mbar_wait_parked(umma::smem_u32(&bars[1]), (uint32_t)(g & 1), kPollLimit, kPollHintNs)) {
+        const bool mma_ok = umma::mbar_wait_parked(umma::smem_u32(&bars[1]), (uint32_t)(g & 1), a.poll_limit, kPollHintNs);
+        if (!mma_ok) {
           set_status(a.e.status, TNMC_E_TIMEOUT);
           misc[1] = 1;
         }
         umma::fence_after_sync();
-        if (tid == 0 && issued < total_steps) {
+        if (tid == 0 && mma_ok && misc[2] && issued < total_steps) {
           // the UMMA has read the tile: the next step's tile lands while the epilogue runs
+          // (not after a failed wait: the UMMA, or the tile's own copy, may still use sB)
           umma::mbar_expect_tx(umma::smem_u32(&bars[0]), kStageBytes);
           umma::bulk_g2s(umma::smem_u32(sB), next_tile(), kStageBytes, umma::smem_u32(&bars[0]));
           ++issued;
@@ -323,7 +336,7 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
         } else {
           // ---- left-sweep epilogue: w(s) = f(s) <U[s], R_{c+1}>, draw, Lambda_{c+1} ----
           if (rcopy) {
-            if (!umma::mbar_wait_parked(umma::smem_u32(&bars[2]), nr & 1u, kPollLimit, kPollHintNs)) {
+            if (!umma::mbar_wait_parked(umma::smem_u32(&bars[2]), nr & 1u, a.poll_limit, kPollHintNs)) {
               set_status(a.e.status, TNMC_E_TIMEOUT);
               misc[1] = 1;
             } else if (tid == 0) {
@@ -414,7 +427,21 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
       // end of row: log q, energy, spins; this row becomes the previous row
       if (h == 0) {
         lq += log((double)prod) + (double)pexp * 0.69314718055994530942;
-        E += (double)Erow;
+        if (a.e.integer_couplings) {
+          E += (double)Erow;
+        } else {
+          // the row's terms of eq. ising in FP64 from its spins and the row above
+          for (int c = 0; c < Lx; ++c) {
+            const bool sc = (bits_cur[(c >> 5) * kTile + t] >> (c & 31)) & 1u;
+            double loc = a.h64[(size_t)r * Lx + c];
+            if (c > 0)
+              loc += a.Jh64[(size_t)r * (Lx - 1) + c - 1] *
+                     (((bits_cur[((c - 1) >> 5) * kTile + t] >> ((c - 1) & 31)) & 1u) ? 1.0 : -1.0);
+            if (r > 0)
+              loc += a.Jv64[(size_t)(r - 1) * Lx + c] * (((bits_prev[(c >> 5) * kTile + t] >> (c & 31)) & 1u) ? 1.0 : -1.0);
+            E -= (sc ? 1.0 : -1.0) * loc;
+          }
+        }
         if (active && a.spins_out && !a.spins_in) {
           int8_t* dst = a.spins_out + (size_t)b * n + (size_t)r * Lx;
           if ((Lx & 15) == 0 && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
@@ -445,12 +472,22 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
       if (flag) set_status(a.e.status, TNMC_E_NUMERIC);
     }
   }
-  // teardown: let copies still in flight land (bounded), then free TMEM
+  // teardown (after the last step, or after a wait gave up): let the copies still in
+  // flight land and the last committed UMMA finish (bounded waits with the full limit),
+  // then free TMEM.  Thread 0 observes the tile and R barriers in order and refills a
+  // buffer only after a successful wait, so at most one phase of each is outstanding.
   if (tid == 0) {
-    for (int64_t q = g; q < issued; ++q)
+    // steps thread 0 committed (g counts finished steps; an aborted step committed too),
+    // and tiles it saw land
+    const int64_t committed = g + (abort ? 1 : 0);
+    const int64_t tiles_seen = g + ((abort && misc[2]) ? 1 : 0);
+    for (int64_t q = tiles_seen; q < issued; ++q)
       (void)umma::mbar_wait_parked(umma::smem_u32(&bars[0]), (uint32_t)(q & 1), kPollLimit, kPollHintNs);
     for (uint32_t q = r_done; q < r_issued; ++q)
       (void)umma::mbar_wait_parked(umma::smem_u32(&bars[2]), q & 1u, kPollLimit, kPollHintNs);
+    if (committed > 0)
+      (void)umma::mbar_wait_parked(umma::smem_u32(&bars[1]), (uint32_t)((committed - 1) & 1), kPollLimit,
+                                   kPollHintNs);
     bulk_wait_all();
   }
   umma::fence_before_sync();
@@ -576,6 +613,16 @@ tnmc_status tnmc_launch_sample_tc(const tnmc_env* env, int64_t B, uint64_t seed,
   a.energy = energy;
   a.flags = flags;
   a.stack = static_cast<float4*>(me->scratch.ptr);
+  a.h64 = d.h;
+  a.Jh64 = d.Jh;
+  a.Jv64 = d.Jv;
+  a.poll_limit = kPollLimit;
+  {
+    // test hook: TNMC_DEBUG_POLL_LIMIT=<n> caps the polls of the in-loop waits (0: they
+    // give up at once), so that the timeout path can be exercised without a stuck copy
+    const char* pl = getenv("TNMC_DEBUG_POLL_LIMIT");
+    if (pl && *pl) a.poll_limit = (uint32_t)strtoul(pl, nullptr, 10);
+  }
   sample_tc_kernel<<<(unsigned)grid, kThreads, smem, stream>>>(a);
   TNMC_CUDA_TRY(cudaGetLastError());
   return TNMC_OK;
