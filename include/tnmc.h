@@ -263,6 +263,22 @@ tnmc_status tnmc_logq_backward(const tnmc_env* env, int64_t B, const int8_t* spi
 tnmc_status tnmc_env_get_params(const tnmc_env* env, float* dst, void* stream);
 tnmc_status tnmc_env_set_params(tnmc_env* env, const float* src, void* stream);
 
+/*
+ * Replace the FP64 environment tensors M^(r)_c the samplers use, and re-derive every
+ * sampler copy the env holds (FP64 transposed, FP32, BF16 operand tiles) from them.
+ * The builder's other outputs (log Z~, log-scales, singular values) are kept.  Any
+ * normalisation of the tensors gives a valid proposal: each conditional is
+ * normalised by w_+ + w_- (Sec. 2, eq. pi-approx), so q sums to one whatever the
+ * tensors are.  This serves environments made elsewhere (another compression of
+ * App. A, a tuned FP64 set) and tests that run the samplers on given tensors.
+ * src     [Ly][Lx][P][2][P] doubles, M^(r)_c[a][sigma][b], ZERO outside the bond
+ *         dimensions chi_c^(r) x 2 x chi_{c+1}^(r) (P from tnmc_env_info); host or
+ *         device memory (copied with cudaMemcpyAsync, kind default).
+ * Asynchronous on `stream`; a host `src` must stay valid until the stream reaches
+ * the copy.
+ */
+tnmc_status tnmc_env_set_tensors(tnmc_env* env, const double* src, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Batched persistent form: many independent instances (for instance disorder
  * realisations of uneven L and chi) in single launches.  Each instance follows

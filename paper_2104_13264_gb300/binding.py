@@ -62,6 +62,7 @@ SIGNATURES = {
     "tnmc_logq_backward": ([_P, _I64, _P, _P, _P, _P], _INT),
     "tnmc_env_get_params": ([_P, _P, _P], _INT),
     "tnmc_env_set_params": ([_P, _P, _P], _INT),
+    "tnmc_env_set_tensors": ([_P, _P, _P], _INT),
     "tnmc_build_env_batched": ([_INT, _P, _P, _P, _INT, _P, _P], _INT),
     "tnmc_batch_create": ([_INT, _P, _P, _I64, _INT, _INT, _INT, _P, ctypes.POINTER(_P)], _INT),
     "tnmc_batch_free": ([_P], _INT),
@@ -275,6 +276,14 @@ def set_params(env, params, stream=None):
     p = params.detach().contiguous()
     assert p.dtype.is_floating_point and p.numel() == param_count(env)
     _check(lib().tnmc_env_set_params(env.handle, _ptr(p.float()), _stream(stream)))
+
+
+def set_tensors(env, tensors, stream=None):
+    """Replace the FP64 tensors ([Ly][Lx][P][2][P], zero outside the bond dimensions; a
+    float64 torch tensor on the device) and re-derive every sampler copy."""
+    t = tensors.detach().contiguous()
+    assert t.dtype == __import__("torch").float64 and t.is_cuda and t.numel() == param_count(env)
+    _check(lib().tnmc_env_set_tensors(env.handle, _ptr(t), _stream(stream)))
 
 
 def logq_backward(env, spins, weights, stream=None):

@@ -459,6 +459,15 @@ tnmc_status tnmc_env_get_params(const tnmc_env* env, float* dst, void* stream) {
   return TNMC_OK;
 }
 
+tnmc_status tnmc_env_set_tensors(tnmc_env* env, const double* src, void* stream) {
+  g_err[0] = 0;
+  CHECK_ARG(env && src, "env and src must be non-null");
+  const size_t n = (size_t)env->d.Lx * env->d.Ly * env->d.P * 2 * env->d.P;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  TNMC_CUDA_TRY(cudaMemcpyAsync(const_cast<double*>(env->d.M64), src, n * sizeof(double), cudaMemcpyDefault, s));
+  return env_derive(env, s);
+}
+
 tnmc_status tnmc_env_set_params(tnmc_env* env, const float* src, void* stream) {
   g_err[0] = 0;
   CHECK_ARG(env && src, "env and src must be non-null");

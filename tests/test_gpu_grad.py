@@ -2,7 +2,9 @@
 
 The gradient depends on the gauge of the tensors, so both sides get the same
 seeded random tensors from the input generator (not builder output): the GPU
-through tnmc_env_set_params, the oracle as its Env.M.  Bar: 1e-3 relative.
+through tnmc_env_set_params, the oracle as its Env.M.  Bar: 1e-3 relative, per site
+(Frobenius norm of each site's gradient), and for directional derivatives against
+the oracle's central differences at the 64 x 64, chi = 32 tuning shape.
 """
 import numpy as np
 import pytest
@@ -62,14 +64,22 @@ def test_grad_matches_oracle(B, idx):
     glq = B.logq(env, spins, precision="f32")[0].cpu().numpy()
     np.testing.assert_allclose(glq, olq, rtol=1e-4)
     g = B.logq_backward(env, spins, torch.from_numpy(w).float().cuda()).cpu().numpy().reshape(inst.Ly, inst.Lx, P, 2, P)
-    scale = max(np.abs(G[r][c]).max() for r in range(inst.Ly) for c in range(inst.Lx))
+    gmax = max(np.linalg.norm(G[r][c]) for r in range(inst.Ly) for c in range(inst.Lx))
+    worst = 0.0
     for r in range(inst.Ly):
         for c in range(inst.Lx):
             ref = G[r][c]
             got = g[r, c, :ref.shape[0], :, :ref.shape[2]]
-            assert np.abs(got - ref).max() <= 1e-3 * scale, (r, c)
+            # each site on its own: 1e-3 relative in the Frobenius norm; the floor only
+            # matters for a site whose gradient is essentially zero (FP32 sums of terms
+            # of size ~gmax cannot resolve it to 1e-3 of itself)
+            d, nref = np.linalg.norm(got - ref), np.linalg.norm(ref)
+            assert d <= 1e-3 * nref + 1e-7 * gmax, (r, c, d, nref, gmax)
+            if nref > 1e-3 * gmax:
+                worst = max(worst, d / nref)
             # entries outside the bond dimensions stay zero
             assert np.all(g[r, c, ref.shape[0]:] == 0) and np.all(g[r, c, :, :, ref.shape[2]:] == 0)
+    print("case %d: worst per-site relative gradient error %.3g (bar 1e-3)" % (idx, worst))
 
 
 def test_autograd_function(B):
@@ -97,6 +107,41 @@ def test_gradient_identities_at_config4_size(B):
     gs = (g * M).view(inst.Ly * inst.Lx, -1).sum(dim=1)
     gn = (g.abs() * M.abs()).view(inst.Ly * inst.Lx, -1).sum(dim=1)
     assert torch.all(gs.abs() <= 1e-3 * gn + 1e-6)
+
+
+def test_config4_directional_derivatives_vs_central_differences(B):
+    """64 x 64 Villain lattice at chi = 32 (the tuning workload's shape): for three random
+    directions D on three sites, <G, D> from tnmc_logq_backward against the oracle's FP64
+    central difference (F(M + hD) - F(M - hD)) / 2h of F = mean log q, both on the same
+    seeded FP32-representable tensors.  Bar: 1e-3 relative."""
+    inst = instances.config4()
+    Lx, Ly, chi = inst.Lx, inst.Ly, inst.chi
+    shapes = [(tnmc.bond_dim(chi, Lx, Ly, r, c), 2, tnmc.bond_dim(chi, Lx, Ly, r, c + 1))
+              for r in range(Ly) for c in range(Lx)]
+    ts = [t.astype(np.float32).astype(np.float64) for t in instances.random_tensors(shapes, seed=44)]
+    oenv = tnmc.Env(Lx, Ly, inst.beta, chi, inst.Jh, inst.Jv, inst.h)
+    oenv.M = [[ts[r * Lx + c] for c in range(Lx)] for r in range(Ly)]
+    env = B.Env.from_instance(inst, precisions=("f64", "f32"))
+    flat, P = _flat(env, ts, inst)
+    B.set_params(env, torch.from_numpy(flat.reshape(-1)).cuda())
+    n = 128
+    osp, _, _, ofl = tnmc.sample(oenv, n, seed=3)
+    assert np.all(ofl == 0)
+    w = np.full(n, 1.0 / n)
+    g = B.logq_backward(env, torch.from_numpy(osp).cuda(), torch.from_numpy(w).float().cuda())
+    g = g.cpu().numpy().astype(np.float64).reshape(Ly, Lx, P, 2, P)
+    rng = np.random.default_rng(7)
+    for r, c in [(0, 5), (31, 32), (63, 60)]:
+        M = oenv.M[r][c]
+        D = rng.standard_normal(M.shape)
+        h = 1e-5 * np.abs(M).max() / np.abs(D).max()
+        fp = np.dot(w, tnmc.logq_at(oenv, osp, r, c, h * D))
+        fm = np.dot(w, tnmc.logq_at(oenv, osp, r, c, -h * D))
+        fd = (fp - fm) / (2 * h)
+        got = float(np.sum(g[r, c, :M.shape[0], :, :M.shape[2]] * D))
+        print("site (%d, %d): <G, D> = %.9g, central difference %.9g, rel %.3g" % (r, c, got, fd, abs(got - fd) / abs(fd)))
+        assert abs(got - fd) <= 1e-3 * abs(fd), (r, c, got, fd)
+    env.free()
 
 
 def test_tuning_raises_mean_logq(B):
