@@ -57,6 +57,7 @@ class Env:
         self.sv = {}                    # (r, c) -> kept singular values / 2-norm of all
         self.discarded = {}             # (r, c) -> discarded squared weight fraction
         self.logZ = float("nan")
+        self.Mr = None                  # optional Mr[r][c][u]: right-sweep tensors (env_bf16)
 
 
 def _check_lattice(Jh, Jv, h):
@@ -172,11 +173,27 @@ def split_bf16(x):
     return hi + round_bf16(np.asarray(x, dtype=np.float64) - hi)
 
 
+def field_combined(env, r, c):
+    """Mt^(u)[a, b] = sum_sigma f_u(sigma) M^(r)_c[a, sigma, b] for u = -1, +1 (index 0, 1):
+    the site tensor with the field of the spin above (value u) applied, f_u(sigma) =
+    exp(beta Jv[r-1, c] u sigma), 1 on row 0.  The right-sweep recursion of one sample
+    is R_c = Mt^(u) R_{c+1} with u its spin above (Sec. 2, eq. pi-approx; App. A: the
+    rows above are a product state)."""
+    M = env.M[r][c]
+    if r == 0:
+        t = M[:, 0, :] + M[:, 1, :]
+        return np.stack([t, t])
+    f = np.exp(env.beta * env.Jv[r - 1, c] * np.outer(SPIN, SPIN))       # f[u, sigma]
+    return np.einsum("us,asb->uab", f, M)
+
+
 def env_bf16(env):
-    """Copy of env with every tensor entry replaced by its BF16 hi + lo pair (the
-    operands of the tensor-core contraction)."""
+    """The environment as the tensor-core contraction sees it: every entry of M (left
+    sweep) and of the field-combined right-sweep tensors Mt^(u) (formed in FP64) replaced
+    by its BF16 hi + lo pair."""
     out = Env(env.Lx, env.Ly, env.beta, env.chi, env.Jh, env.Jv, env.h)
     out.M = [[split_bf16(t) for t in row] for row in env.M]
+    out.Mr = [[split_bf16(field_combined(env, r, c)) for c in range(env.Lx)] for r in range(env.Ly)]
     out.log_scale, out.log_lambda, out.logZ = env.log_scale, env.log_lambda, env.logZ
     return out
 
@@ -228,9 +245,15 @@ def run(env, B, seed=0, sample_offset=0, forced=None, keep=False, samples=None):
             f = row_fields(env, spins, r)
             R = [None] * (Lx + 1)
             R[Lx] = np.ones((B, 1))
+            up = (spins[:, r - 1, :] > 0).astype(np.int64) if r > 0 else np.zeros((B, Lx), dtype=np.int64)
             for c in range(Lx - 1, 0, -1):
-                Y = np.einsum("asb,nb->nas", M[c], R[c + 1])
-                R[c] = _pow2_normalize(Y[:, :, 0] * f[:, c, 0:1] + Y[:, :, 1] * f[:, c, 1:2])
+                if env.Mr is None:
+                    Y = np.einsum("asb,nb->nas", M[c], R[c + 1])
+                    R[c] = _pow2_normalize(Y[:, :, 0] * f[:, c, 0:1] + Y[:, :, 1] * f[:, c, 1:2])
+                else:
+                    # the same recursion with the field-combined tensor of each sample's
+                    # spin above, as given (the rounded tensors of env_bf16)
+                    R[c] = _pow2_normalize(np.einsum("nab,nb->na", env.Mr[r][c][up[:, c]], R[c + 1]))
             Lam = [None] * (Lx + 1)
             Lam[0] = np.ones((B, 1))
             wraw = np.zeros((B, Lx, 2))

@@ -4,8 +4,10 @@
 //
 // A CTA owns a tile of 128 samples (UMMA M = 128): sample t is TMEM lane t.  Per
 // site one UMMA 128 x 128 x 64 forms, for all samples at once,
-//   right sweep  D[t][(s, a)] = sum_b R_{c+1}[t][b] M_c[a][s][b]   -> R_c = f(-) D(-) + f(+) D(+)
-//   left sweep   D[t][(s, b)] = sum_a Lambda_c[t][a] M_c[a][s][b]  -> U[s] = D(s)
+//   right sweep  D[t][(u, a)] = sum_b R_{c+1}[t][b] Mt^(u)_c[a][b]   -> R_c = D(u_t, -)
+//   left sweep   D[t][(s, b)] = sum_a Lambda_c[t][a] M_c[a][s][b]     -> U[s] = D(s, -)
+// where Mt^(u) = sum_s f_u(s) M[:, s, :] is the site tensor with the field factor of the
+// spin above (u) already applied (both u at once; the epilogue keeps the sample's own),
 // with the vectors (A operand, 128 x 64) in shared memory and the environment tile
 // (B operand, 128 x 64) loaded from a pre-swizzled copy of the environment.  Both
 // operands are BF16 hi + lo pairs; the three products hi*hi + lo*hi + hi*lo keep
@@ -13,9 +15,12 @@
 //
 // 256 threads: thread (t, h) = (tid % 128, tid / 128) runs the epilogue of sample t
 // for the components k in [32h, 32h + 32) -- warps w and w + 4 read the same TMEM
-// lanes (lane quadrant w % 4) at different columns.  The two halves exchange their
-// partial dot products and maxima through shared memory under a named barrier per
-// warp pair, and take identical decisions from identical sums.
+// lanes (lane quadrant w % 4) at different columns, 16 columns per load.  The two
+// halves exchange their partial maxima (right steps) or partial dot products (left
+// steps) through shared memory under a named barrier per warp pair, and take
+// identical decisions from identical sums.  Every rescaling is by a power of two,
+// which leaves the arithmetic of q unchanged: right vectors by their max, left vectors
+// by the drawn weight w(s) (which the left step has already summed).
 //
 // The left sweep needs R_{c+1} in the reverse of the order the right sweep makes it:
 // the right sweep writes every R_c into a shared buffer, from which one 32 KB bulk store
@@ -70,24 +75,28 @@ struct TcArgs {
 __device__ inline float pow2f(int e) { return __int_as_float((e + 127) << 23); }   // 2^e, |e| < 127
 __device__ inline int ilogb_f(float x) { return ((__float_as_int(x) >> 23) & 0xff) - 127; }   // x normal, > 0
 
+// Split 8 FP32 values (components k0 .. k0+7, k0 a multiple of 8) into BF16 hi + lo and
+// store them in row t of the two swizzled A operands (one 16-byte chunk each).
+__device__ inline void store_split8(unsigned char* sHi, unsigned char* sLo, int t, int k0, const float* v) {
+  uint32_t wh[4], wl[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float x0 = v[2 * q], x1 = v[2 * q + 1];
+    const __nv_bfloat162 h2 = __floats2bfloat162_rn(x0, x1);
+    const __nv_bfloat162 l2 = __floats2bfloat162_rn(x0 - __low2float(h2), x1 - __high2float(h2));
+    wh[q] = *reinterpret_cast<const uint32_t*>(&h2);
+    wl[q] = *reinterpret_cast<const uint32_t*>(&l2);
+  }
+  const uint32_t off = umma::sw128_offset(t, k0);
+  *reinterpret_cast<uint4*>(sHi + off) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
+  *reinterpret_cast<uint4*>(sLo + off) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
+}
+
 // Split 32 FP32 values (components 32h .. 32h+31) into BF16 hi + lo and store them in
 // row t of the two swizzled A operands.
 __device__ inline void store_split_half(unsigned char* sHi, unsigned char* sLo, int t, int h, const float* v) {
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    uint32_t wh[4], wl[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const float x0 = v[8 * j + 2 * q], x1 = v[8 * j + 2 * q + 1];
-      const __nv_bfloat162 h2 = __floats2bfloat162_rn(x0, x1);
-      const __nv_bfloat162 l2 = __floats2bfloat162_rn(x0 - __low2float(h2), x1 - __high2float(h2));
-      wh[q] = *reinterpret_cast<const uint32_t*>(&h2);
-      wl[q] = *reinterpret_cast<const uint32_t*>(&l2);
-    }
-    const uint32_t off = umma::sw128_offset(t, 32 * h + 8 * j);
-    *reinterpret_cast<uint4*>(sHi + off) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
-    *reinterpret_cast<uint4*>(sLo + off) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
-  }
+  for (int j = 0; j < 4; ++j) store_split8(sHi, sLo, t, 32 * h + 8 * j, v + 8 * j);
 }
 
 // e_0 restricted to this thread's half
@@ -120,9 +129,12 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
   unsigned char* sB = base + 2 * kVecBytes;                                   // environment tile (hi, lo)
   float4* sR = reinterpret_cast<float4*>(sB + kStageBytes);                  // [2][8][128] float4
   uint64_t* bars = reinterpret_cast<uint64_t*>(sB + kStageBytes + kRBytes);  // [0] tile, [1] UMMA, [2] R
-  uint32_t* misc = reinterpret_cast<uint32_t*>(bars + 3);                    // [0] tmem base, [1] abort
-  float* xw = reinterpret_cast<float*>(misc + 4);   // [2 halves][4][128]: partial w(-), w(+), max|U(-)|, max|U(+)|
-  float* xm = xw;                                   // right steps: [2 halves][128] partial max
+  uint32_t* misc = reinterpret_cast<uint32_t*>(bars + 3);                    // [0] tmem base, [1] abort, [2] tile ok
+  // thread 0's copy counters live in shared memory (registers are the scarce resource):
+  // [0] environment tiles copied, [1] R copies issued, [2] R copies waited for
+  int64_t* cnt = reinterpret_cast<int64_t*>(misc + 4);
+  float* xw = reinterpret_cast<float*>(misc + 10);   // left steps: [2 halves][2][128] partial w(-), w(+)
+  float* xmb = xw + 4 * kTile;                      // right steps: [2 steps][2 halves][128] partial max
   const int Lx = a.e.Lx, Ly = a.e.Ly;
   const int W = (Lx + 31) >> 5;
   uint32_t* xs = reinterpret_cast<uint32_t*>(xw + 8 * kTile);   // [2][128]: the site's 64-bit uniform
@@ -148,6 +160,7 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
     umma::fence_mbar_init();
     misc[1] = 0;
     misc[2] = 1;
+    cnt[0] = cnt[1] = cnt[2] = 0;
   }
   umma::fence_before_sync();
   __syncthreads();
@@ -167,13 +180,12 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
     }
     return T;
   };
-  int64_t issued = 0;               // environment tiles copied (thread 0)
-  uint32_t r_issued = 0, r_done = 0; // R copies issued / waited for (thread 0)
+
   uint32_t nr = 0;                   // R copies consumed (every thread)
   if (tid == 0 && total_steps > 0) {
     umma::mbar_expect_tx(umma::smem_u32(&bars[0]), kStageBytes);
     umma::bulk_g2s(umma::smem_u32(sB), next_tile(), kStageBytes, umma::smem_u32(&bars[0]));
-    issued = 1;
+    cnt[0] = 1;
   }
 
   int64_t g = 0;
@@ -201,11 +213,12 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
             if (src[c] > 0) bits_cur[(c >> 5) * kTile + t] |= 1u << (c & 31);
         }
       }
-      // row start: A = R_{Lx} = e_0 (Lx > 1) or Lambda_0 = e_0 (Lx = 1)
+      // row start: A = R_{Lx} = e_0 (Lx > 1) or Lambda_0 = e_0 (Lx = 1), whose max is 1
       {
         float v[32];
         unit_half(v, h);
         store_split_half(sHi, sLo, t, h, v);
+        xmb[((g + 1) & 1) * (2 * kTile) + h * kTile + t] = 1.0f;
       }
       float prod = 1.0f;
       int pexp = 0;
@@ -226,7 +239,7 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
             umma::mbar_expect_tx(umma::smem_u32(&bars[2]), kRBytes);
             umma::bulk_g2s(umma::smem_u32(sR), stk_cta + (size_t)(c + 1) * (2 * 8 * kTile), kRBytes,
                            umma::smem_u32(&bars[2]));
-            ++r_issued;
+            ++cnt[1];
           }
           const bool tile_ok = umma::mbar_wait_parked(umma::smem_u32(&bars[0]), (uint32_t)(g & 1), a.poll_limit,
                                                       kPollHintNs);
@@ -299,40 +312,50 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
           misc[1] = 1;
         }
         umma::fence_after_sync();
-        if (tid == 0 && mma_ok && misc[2] && issued < total_steps) {
+        if (tid == 0 && mma_ok && misc[2] && cnt[0] < total_steps) {
           // the UMMA has read the tile: the next step's tile lands while the epilogue runs
           // (not after a failed wait: the UMMA, or the tile's own copy, may still use sB)
           umma::mbar_expect_tx(umma::smem_u32(&bars[0]), kStageBytes);
           umma::bulk_g2s(umma::smem_u32(sB), next_tile(), kStageBytes, umma::smem_u32(&bars[0]));
-          ++issued;
+          ++cnt[0];
         }
-        uint32_t u0[32], u1[32];
-        umma::tmem_ld32_issue(tlane, u0);        // s = -1, this half
-        umma::tmem_ld32_issue(tlane + 64, u1);   // s = +1, this half
-        umma::tmem_wait_ld();
-        umma::tmem_hold(u0);
-        umma::tmem_hold(u1);
         float v[32];
         if (!left) {
-          // ---- right-sweep epilogue: R_c = f(-) D(-, a) + f(+) D(+, a), rescaled ----
+          // ---- right-sweep epilogue: R_c = Mt^(u)_c R_{c+1} for this sample's u (the spin
+          // above): the UMMA formed both u halves, the epilogue selects one ----
+          const uint32_t col = up ? 1u : 0u;
+          uint32_t d0[16], d1[16], e0[16], e1[16];
+          umma::tmem_ld16_issue(tlane, d0);
+          umma::tmem_ld16_issue(tlane + 16, d1);
+          umma::tmem_ld16_issue(tlane + 64, e0);
+          umma::tmem_ld16_issue(tlane + 80, e1);
+          // the power of two that rescales R_c comes from the full max of the previous A
+          // operand (both halves' partial maxima, exchanged through the step barrier), so no
+          // pair barrier is needed here: A(c) = raw_c 2^(-ilogb(max |A(c+1)|)) stays within
+          // one step's growth of [1, 2)
+          const float* mrd = xmb + ((g + 1) & 1) * (2 * kTile);   // written by the previous step
+          const float mprev = fmaxf(mrd[t], mrd[kTile + t]);
+          const float sc = (mprev > 0x1.0p-126f && mprev < INFINITY) ? pow2f(-ilogb_f(mprev)) : 1.0f;
+          umma::tmem_wait_ld();
+          umma::tmem_hold16(d0);
+          umma::tmem_hold16(d1);
+          umma::tmem_hold16(e0);
+          umma::tmem_hold16(e1);
           float m4[4] = {0.0f, 0.0f, 0.0f, 0.0f};   // four independent chains (max is exact)
 #pragma unroll
-          for (int q = 0; q < 32; ++q) {
-            v[q] = fm * __uint_as_float(u0[q]) + fp * __uint_as_float(u1[q]);
-            m4[q & 3] = fmaxf(m4[q & 3], fabsf(v[q]));
+          for (int q = 0; q < 16; ++q) {
+            v[q] = __uint_as_float(col ? e0[q] : d0[q]) * sc;
+            v[16 + q] = __uint_as_float(col ? e1[q] : d1[q]) * sc;
+            m4[q & 3] = fmaxf(m4[q & 3], fmaxf(fabsf(v[q]), fabsf(v[16 + q])));
           }
-          float mx = fmaxf(fmaxf(m4[0], m4[1]), fmaxf(m4[2], m4[3]));
-          xm[h * kTile + t] = mx;
-          pair_sync(warp);
-          mx = fmaxf(xm[t], xm[kTile + t]);
-          const float sc = (mx > 0.0f && mx < INFINITY) ? pow2f(-ilogb_f(mx)) : 1.0f;
-#pragma unroll
-          for (int q = 0; q < 32; ++q) v[q] *= sc;
           float4* dst = sR + h * (8 * kTile) + t;   // to the stack by a bulk store next step
 #pragma unroll
           for (int j = 0; j < 8; ++j) dst[j * kTile] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
           if (c == 1) unit_half(v, h);           // the left sweep starts from Lambda_0 = e_0
           store_split_half(sHi, sLo, t, h, v);
+          // this half's max of the new A operand, read by both halves in the next step (the
+          // buffers alternate by step, so this write cannot meet this step's reads)
+          xmb[(g & 1) * (2 * kTile) + h * kTile + t] = fmaxf(fmaxf(m4[0], m4[1]), fmaxf(m4[2], m4[3]));
         } else {
           // ---- left-sweep epilogue: w(s) = f(s) <U[s], R_{c+1}>, draw, Lambda_{c+1} ----
           if (rcopy) {
@@ -340,43 +363,46 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
               set_status(a.e.status, TNMC_E_TIMEOUT);
               misc[1] = 1;
             } else if (tid == 0) {
-              ++r_done;
+              ++cnt[2];
             }
             ++nr;
           }
-          // partial dot products over this half, in four interleaved chains; R_{c+1} is
-          // read from the shared buffer chunk by chunk (e_0 at the right end of the row)
-          // (and the maxima of |U(-)|, |U(+)| over this half, so that one exchange serves
-          // both the conditional and the rescaling of Lambda_{c+1})
+          // pass 1: partial dot products over this half, 16 components at a time
           float a0[4] = {0.0f, 0.0f, 0.0f, 0.0f}, a1[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-          float n0 = 0.0f, n1 = 0.0f;
           const float4* src = sR + h * (8 * kTile) + t;
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            float4 q4 = make_float4((h == 0 && j == 0) ? 1.0f : 0.0f, 0.0f, 0.0f, 0.0f);
-            if (c + 1 < Lx) q4 = src[j * kTile];
-            const float r4[4] = {q4.x, q4.y, q4.z, q4.w};
+          for (int ch = 0; ch < 2; ++ch) {
+            uint32_t p0[16], p1[16];
+            umma::tmem_ld16_issue(tlane + 16 * ch, p0);
+            umma::tmem_ld16_issue(tlane + 64 + 16 * ch, p1);
+            umma::tmem_wait_ld();
+            umma::tmem_hold16(p0);
+            umma::tmem_hold16(p1);
 #pragma unroll
-            for (int z = 0; z < 4; ++z) {
-              const float x0 = __uint_as_float(u0[4 * j + z]), x1 = __uint_as_float(u1[4 * j + z]);
-              a0[z] = fmaf(x0, r4[z], a0[z]);
-              a1[z] = fmaf(x1, r4[z], a1[z]);
-              n0 = fmaxf(n0, fabsf(x0));
-              n1 = fmaxf(n1, fabsf(x1));
+            for (int j = 0; j < 4; ++j) {
+              float4 q4 = make_float4((h == 0 && ch == 0 && j == 0) ? 1.0f : 0.0f, 0.0f, 0.0f, 0.0f);
+              if (c + 1 < Lx) q4 = src[(4 * ch + j) * kTile];
+              const float r4[4] = {q4.x, q4.y, q4.z, q4.w};
+#pragma unroll
+              for (int z = 0; z < 4; ++z) {
+                a0[z] = fmaf(__uint_as_float(p0[4 * j + z]), r4[z], a0[z]);
+                a1[z] = fmaf(__uint_as_float(p1[4 * j + z]), r4[z], a1[z]);
+              }
             }
           }
-          xw[(4 * h) * kTile + t] = (a0[0] + a0[1]) + (a0[2] + a0[3]);
-          xw[(4 * h + 1) * kTile + t] = (a1[0] + a1[1]) + (a1[2] + a1[3]);
-          xw[(4 * h + 2) * kTile + t] = n0;
-          xw[(4 * h + 3) * kTile + t] = n1;
+          xw[(2 * h) * kTile + t] = (a0[0] + a0[1]) + (a0[2] + a0[3]);
+          xw[(2 * h + 1) * kTile + t] = (a1[0] + a1[1]) + (a1[2] + a1[3]);
           if (h == 0) {
             xs[t] = (uint32_t)x;
             xs[kTile + t] = (uint32_t)(x >> 32);
           }
+          uint32_t p0[16], p1[16];
+          umma::tmem_ld16_issue(tlane, p0);
+          umma::tmem_ld16_issue(tlane + 64, p1);
           pair_sync(warp);
           if (h == 1) x = (uint64_t)xs[t] | ((uint64_t)xs[kTile + t] << 32);
-          float w0 = xw[t] + xw[4 * kTile + t];            // half 0 + half 1, same order in both
-          float w1 = xw[kTile + t] + xw[5 * kTile + t];
+          float w0 = xw[t] + xw[2 * kTile + t];            // half 0 + half 1, same order in both
+          float w1 = xw[kTile + t] + xw[3 * kTile + t];
           w0 = fmaxf(w0 * fm, 0.0f);
           w1 = fmaxf(w1 * fp, 0.0f);
           const float tot = w0 + w1;
@@ -403,22 +429,30 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
             Erow -= (plus ? 1.0f : -1.0f) * loc;
             s_left = plus;
           }
-          // Lambda_{c+1} = f(s) U[s], rescaled; max |f(s) U[s]| = f(s) max |U[s]| (fs > 0,
-          // rounding is monotone), so the exchanged maxima give the scale directly
-          const float fs = plus ? fp : fm;
-          const float mraw = plus ? fmaxf(xw[3 * kTile + t], xw[7 * kTile + t]) : fmaxf(xw[2 * kTile + t], xw[6 * kTile + t]);
-          const float mx = mraw * fs;
+          // Lambda_{c+1} = f(s) U[s] times a power of two: any such factor leaves q's
+          // arithmetic unchanged, so it is taken from w(s) = f(s) <U[s], R_{c+1}> (already
+          // summed) rather than from max |U[s]|: <Lambda_{c+1}, R_{c+1}> lands in [1, 2)
+          const float ws = plus ? w1 : w0;
+          const float mult = (plus ? fp : fm) * ((ws > 0x1.0p-126f && ws < INFINITY) ? pow2f(-ilogb_f(ws)) : 1.0f);
+          umma::tmem_wait_ld();
+          umma::tmem_hold16(p0);
+          umma::tmem_hold16(p1);
 #pragma unroll
-          for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(plus ? u1[q] : u0[q]) * fs;
-          const float sc = (mx > 0.0f && mx < INFINITY) ? pow2f(-ilogb_f(mx)) : 1.0f;
+          for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(plus ? p1[q] : p0[q]) * mult;
+          umma::tmem_ld16_issue(tlane + 16, p0);
+          umma::tmem_ld16_issue(tlane + 80, p1);
+          umma::tmem_wait_ld();
+          umma::tmem_hold16(p0);
+          umma::tmem_hold16(p1);
 #pragma unroll
-          for (int q = 0; q < 32; ++q) v[q] *= sc;
+          for (int q = 0; q < 16; ++q) v[16 + q] = __uint_as_float(plus ? p1[q] : p0[q]) * mult;
           store_split_half(sHi, sLo, t, h, v);
         }
         // the shared A operand and R buffer become visible to the UMMA and the bulk store
         umma::fence_proxy_async();
         umma::fence_before_sync();
         __syncthreads();
+
         if (misc[1]) {
           abort = true;
           break;
@@ -481,10 +515,10 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
     // and tiles it saw land
     const int64_t committed = g + (abort ? 1 : 0);
     const int64_t tiles_seen = g + ((abort && misc[2]) ? 1 : 0);
-    for (int64_t q = tiles_seen; q < issued; ++q)
+    for (int64_t q = tiles_seen; q < cnt[0]; ++q)
       (void)umma::mbar_wait_parked(umma::smem_u32(&bars[0]), (uint32_t)(q & 1), kPollLimit, kPollHintNs);
-    for (uint32_t q = r_done; q < r_issued; ++q)
-      (void)umma::mbar_wait_parked(umma::smem_u32(&bars[2]), q & 1u, kPollLimit, kPollHintNs);
+    for (int64_t q = cnt[2]; q < cnt[1]; ++q)
+      (void)umma::mbar_wait_parked(umma::smem_u32(&bars[2]), (uint32_t)(q & 1), kPollLimit, kPollHintNs);
     if (committed > 0)
       (void)umma::mbar_wait_parked(umma::smem_u32(&bars[1]), (uint32_t)((committed - 1) & 1), kPollLimit,
                                    kPollHintNs);
@@ -496,8 +530,11 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
   if (warp == 0) umma::tmem_dealloc(tmem, kN);
 }
 
-// Pre-swizzled BF16 operand tiles of every (r, c): right-sweep (n = s*64 + a, k = b)
-// and left-sweep (n = s*64 + b, k = a), zero outside the bond dimensions.
+// Pre-swizzled BF16 operand tiles of every (r, c).  Left sweep: M itself (n = s*64 + b,
+// k = a).  Right sweep: the field-combined tensor of each value u of the spin above,
+//   Mt^(u)[a][b] = sum_s f_u(s) M[a][s][b],  f_u(s) = exp(beta Jv[r-1][c] u s)  (1 on row 0),
+// formed in FP64 (n = u*64 + a, k = b), so that R_c = Mt^(u) R_{c+1} is one half of the
+// UMMA output.  Both are zero outside the bond dimensions and stored as BF16 hi + lo.
 __global__ void derive_tc_kernel(DeviceEnv e, __nv_bfloat16* TR, __nv_bfloat16* TL, size_t ntens) {
   const int P = e.P;
   const size_t per = (size_t)kN * kK;
@@ -508,8 +545,13 @@ __global__ void derive_tc_kernel(DeviceEnv e, __nv_bfloat16* TR, __nv_bfloat16* 
     const int nn = rem / kK, k = rem % kK;
     const int s = nn >> 6, x = nn & 63;
     const double* M = e.M64 + tt * (size_t)P * 2 * P;
-    // right tile: a = x, b = k ; left tile: b = x, a = k
-    const double vr = (x < P && k < P) ? M[((size_t)x * 2 + s) * P + k] : 0.0;
+    const double fmin = e.fe[2 * tt], fplus = e.fe[2 * tt + 1];   // exp(-beta Jv), exp(+beta Jv); 1 on row 0
+    // right tile: u = s (0: spin above -1), a = x, b = k ; left tile: s, b = x, a = k
+    double vr = 0.0;
+    if (x < P && k < P) {
+      const double m0 = M[((size_t)x * 2 + 0) * P + k], m1 = M[((size_t)x * 2 + 1) * P + k];
+      vr = s ? (fmin * m0 + fplus * m1) : (fplus * m0 + fmin * m1);
+    }
     const double vl = (x < P && k < P) ? M[((size_t)k * 2 + s) * P + x] : 0.0;
     // hi = bf16(v), lo = bf16(v - hi): the pair carries about 16 significant bits
     const size_t off = tt * 2 * per + umma::sw128_offset(nn, k) / 2;
@@ -558,7 +600,7 @@ tnmc_status tnmc_launch_sample_tc(const tnmc_env* env, int64_t B, uint64_t seed,
     return TNMC_E_UNSUPPORTED;
   }
   const int W = (d.Lx + 31) / 32;
-  const size_t smem = 1024 + 2 * kVecBytes + kStageBytes + kRBytes + 3 * 8 + 16 +
+  const size_t smem = 1024 + 2 * kVecBytes + kStageBytes + kRBytes + 3 * 8 + 40 +
                       (size_t)10 * kTile * sizeof(float) + (size_t)2 * W * kTile * sizeof(uint32_t);
   int dev = 0, nsm = 0, max_optin = 0;
   TNMC_CUDA_TRY(cudaGetDevice(&dev));
