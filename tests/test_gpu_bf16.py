@@ -122,3 +122,18 @@ def test_bf16_wait_timeout_is_reported_and_context_survives(B, monkeypatch):
         _, olq, oE, ofl = tnmc.logq(ref, sp.cpu().numpy())
         assert np.all(fl.cpu().numpy() == 0)
         np.testing.assert_allclose(lq.cpu().numpy(), olq, rtol=1e-4)
+
+
+def test_bf16_wide_lattice_vs_oracle(B):
+    """A 448-column lattice (14 spin-bit words per sample, the right stack 447 deep)."""
+    inst = instances.ea_pm(3, 448, 1.0, 8, seed=4)
+    ref = tnmc.env_bf16(tnmc.build_env(inst.Jh, inst.Jv, inst.h, inst.beta, inst.chi))
+    env = B.Env.from_instance(inst, precisions=("f64", "bf16"))
+    sp, lq, E, fl = B.sample(env, 333, seed=3, sample_offset=11, precision="bf16")
+    lq2, E2, fl2 = B.logq(env, sp, precision="bf16")
+    torch.cuda.synchronize()
+    assert torch.equal(lq, lq2) and torch.equal(E, E2) and torch.equal(fl, fl2)
+    _, olq, oE, ofl = tnmc.logq(ref, sp.cpu().numpy())
+    assert np.all(fl.cpu().numpy() == 0) and np.all(ofl == 0)
+    np.testing.assert_allclose(lq.cpu().numpy(), olq, rtol=1e-4)
+    assert np.array_equal(E.cpu().numpy(), oE)
