@@ -10,6 +10,8 @@ Stream layout used by the method (the counter's last word names the stream):
              words (0, 1) or (2, 3) as one 64-bit value  x = lo | hi << 32.
   MH         counter (t_lo, t_hi, chain, 1); words (0, 1) -> u = (x >> 11) 2^-53
   init       counter (site // 128, chain_lo, chain_hi, 2); bit (site % 128).
+  sweep      counter (site, chain, sweep, 5); words (0, 1) -> u = (x >> 11) 2^-53
+             (single-spin-flip Metropolis sweeps between proposals)
 The key is the 64-bit seed, (seed_lo, seed_hi).
 """
 import numpy as np
@@ -24,6 +26,7 @@ _S32 = np.uint64(32)
 TAG_DRAW = 0
 TAG_MH = 1
 TAG_INIT = 2
+TAG_SWEEP = 5
 
 
 def philox4x32_10(c0, c1, c2, c3, k0, k1):
@@ -85,3 +88,13 @@ def init_bits(seed, n_sites, chains):
             bit = (words[j // 32] >> np.uint64(j % 32)) & np.uint64(1)
             out[:, s] = np.where(bit == 1, 1, -1)
     return out
+
+
+def sweep_uniform(seed, site, chain, sweep):
+    """Uniform in [0, 1) with 53 random bits for the Metropolis update of `site` in
+    sweep `sweep` of chain `chain` (each a 32-bit counter word; arrays broadcast)."""
+    k0, k1 = _key(seed)
+    w0, w1, _, _ = philox4x32_10(np.asarray(site, dtype=np.uint64), np.asarray(chain, dtype=np.uint64),
+                                 np.asarray(sweep, dtype=np.uint64), np.uint64(TAG_SWEEP), k0, k1)
+    x = w0 | (w1 << _S32)
+    return (x >> np.uint64(11)).astype(np.float64) * 2.0 ** -53

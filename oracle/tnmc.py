@@ -447,3 +447,83 @@ def finite_diff_grad(env, spins, weights, r, c, h_rel=1e-6):
         d[idx] = h
         G[idx] = (np.dot(w, logq_at(env, spins, r, c, d)) - np.dot(w, logq_at(env, spins, r, c, -d))) / (2 * h)
     return G
+
+
+# ---- single-spin-flip Metropolis sweeps and the link-overlap diagnostic (Sec. 3) ----
+
+def local_field(Jh, Jv, h, spins):
+    """h_i + sum_j J_ij s_j for every site of every configuration [C, Ly, Lx] (eq. ising:
+    the energy change of flipping s_i is 2 s_i times it)."""
+    s = np.asarray(spins, dtype=np.float64)
+    Ly, Lx = s.shape[1:]
+    Jh = np.asarray(Jh, dtype=np.float64).reshape(Ly, max(Lx - 1, 0))
+    Jv = np.asarray(Jv, dtype=np.float64).reshape(max(Ly - 1, 0), Lx)
+    f = np.broadcast_to(np.asarray(h, dtype=np.float64), s.shape).copy()
+    if Lx > 1:
+        f[:, :, :-1] += Jh[None] * s[:, :, 1:]     # right neighbour
+        f[:, :, 1:] += Jh[None] * s[:, :, :-1]     # left neighbour
+    if Ly > 1:
+        f[:, :-1, :] += Jv[None] * s[:, 1:, :]     # neighbour below
+        f[:, 1:, :] += Jv[None] * s[:, :-1, :]     # neighbour above
+    return f
+
+
+def metropolis_sweeps(Jh, Jv, h, beta, spins, seed, sweep_offset, sweeps, chain_ids):
+    """`sweeps` checkerboard single-spin-flip Metropolis sweeps of each chain (the sweeps
+    the paper intersperses between proposals, Sec. 3 "Equilibration").
+
+    A sweep updates the sites with (r + c) even, then those with (r + c) odd; sites of
+    one colour have no bond between them, so each is updated against the current
+    values of the other colour.  Site i of chain `chain_ids[b]` in sweep
+    sweep_offset + k flips iff u < exp(-beta dE), dE = 2 s_i (h_i + sum_j J_ij s_j),
+    with u = philox.sweep_uniform(seed, i, chain, sweep).  Returns the new spins.
+    """
+    s = np.array(spins, dtype=np.int8, copy=True)
+    C, Ly, Lx = s.shape
+    chain_ids = np.asarray(chain_ids, dtype=np.uint64)
+    rr, cc = np.meshgrid(np.arange(Ly), np.arange(Lx), indexing="ij")
+    site = (rr * Lx + cc).astype(np.uint64)
+    for k in range(sweeps):
+        sw = np.uint64((sweep_offset + k) & 0xFFFFFFFF)
+        for colour in (0, 1):
+            mask = ((rr + cc) & 1) == colour
+            dE = 2.0 * s.astype(np.float64) * local_field(Jh, Jv, h, s)
+            u = philox.sweep_uniform(seed, site[None, :, :], chain_ids[:, None, None], sw)
+            with np.errstate(over="ignore"):
+                flip = (u < np.exp(-beta * dE)) & mask[None]
+            s = np.where(flip, -s, s).astype(np.int8)
+    return s
+
+
+def link_overlap(Jh, Jv, spins_a, spins_b):
+    """sum over the bonds <ij> of s_i^a s_j^a s_i^b s_j^b for each replica pair (a, b)
+    (the link overlap of Sec. 3, eq. Delta, for one pair of configurations).  Only the
+    lattice's bonds count; J enters only through which bonds exist (all of them)."""
+    a = np.asarray(spins_a, dtype=np.int64)
+    b = np.asarray(spins_b, dtype=np.int64)
+    q = np.zeros(a.shape[0])
+    if a.shape[2] > 1:
+        q += (a[:, :, :-1] * a[:, :, 1:] * b[:, :, :-1] * b[:, :, 1:]).sum(axis=(1, 2))
+    if a.shape[1] > 1:
+        q += (a[:, :-1, :] * a[:, 1:, :] * b[:, :-1, :] * b[:, 1:, :]).sum(axis=(1, 2))
+    return q
+
+
+def n_bonds(Lx, Ly):
+    """|E| of the open-boundary Ly x Lx lattice."""
+    return Ly * (Lx - 1) + (Ly - 1) * Lx
+
+
+def delta_instance(beta, Lx, Ly, mean_energy, mean_link_overlap):
+    """(1/|V|) <H> + (beta/|V|) (|E| - sum_<ij> <s_i s_j>^2) of one instance (Sec. 3, eq.
+    Delta before the disorder average), from a thermal estimate of <H> and of the link
+    overlap (the mean over replica pairs of link_overlap, which estimates sum <s_i s_j>^2)."""
+    return (mean_energy + beta * (n_bonds(Lx, Ly) - mean_link_overlap)) / (Lx * Ly)
+
+
+def delta_from_chains(beta, Lx, Ly, chain_spins, chain_energy):
+    """delta_instance from the C chains of one instance: <H> is the mean of their energies,
+    the link overlap the mean over the replica pairs (2k, 2k + 1)."""
+    sp = np.asarray(chain_spins)
+    q = link_overlap(None, None, sp[0::2], sp[1::2])
+    return delta_instance(beta, Lx, Ly, float(np.mean(chain_energy)), float(np.mean(q)))
