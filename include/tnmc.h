@@ -237,6 +237,36 @@ tnmc_status tnmc_mh_step(const tnmc_env* env, int64_t C, int64_t T, const int8_t
                          void* stream);
 
 /*
+ * Single-spin-flip Metropolis sweeps of chain states, the moves the paper intersperses
+ * between proposals (Sec. 3, "Equilibration"; Table hb: TNMH + Metropolis).  Each of
+ * the C chains gets `sweeps` checkerboard sweeps: first the sites with (r + c) even,
+ * then the odd ones, each updated against the current spins of the other colour.  Site
+ * i flips iff u < exp(-beta dE), dE = 2 s_i (h_i + sum_j J_ij s_j) (eq. ising), with
+ * u = (x >> 11) 2^-53 from Philox words (0, 1) of the counter (i, chain id, sweep, 5):
+ * chain k has id (uint32)(chain_offset + k), and the sweeps are sweep_offset .. +sweeps-1
+ * (low 32 bits).  The sweeps leave the Boltzmann distribution invariant, so a chain that
+ * alternates them with tnmc_mh_step still samples pi exactly.  Afterwards the chains'
+ * log q (sampler copy `precision`) and energy are recomputed, as tnmc_logq does, so the
+ * next MH step sees consistent chain states.
+ * chain_spins   device int8 [C][Ly][Lx], in/out;  chain_logq, chain_energy  device [C], out
+ * The lattice must fit in shared memory (Lx * Ly <= 200 KiB).
+ */
+tnmc_status tnmc_metropolis(const tnmc_env* env, int precision, int64_t C, int8_t* chain_spins, double* chain_logq,
+                            double* chain_energy, uint64_t seed, uint64_t chain_offset, uint64_t sweep_offset,
+                            int sweeps, void* stream);
+
+/*
+ * Link overlap of replica pairs (Sec. 3, eq. Delta): for chains (2k, 2k + 1),
+ *   overlap[k] = sum over the bonds <ij> of s_i^a s_j^a s_i^b s_j^b   (exact integers),
+ * an estimate of sum_<ij> <s_i s_j>^2.  With the chains' mean energy it gives the
+ * equilibration diagnostic (1/|V|)(<H> + beta (|E| - sum_<ij> <s_i s_j>^2)), whose
+ * average over Gaussian disorder vanishes at equilibrium.
+ * C even; chain_spins device int8 [C][Ly][Lx]; overlap device double [C / 2]
+ */
+tnmc_status tnmc_link_overlap(const tnmc_env* env, int64_t C, const int8_t* chain_spins, double* overlap,
+                              void* stream);
+
+/*
  * Gradient of sum_b weights[b] log q(spins[b]) with respect to every tensor of the
  * FP32 sampler copy (the parameters of tnmc_env_get_params), by reverse-mode
  * differentiation of the forced evaluation (Sec. 2, eq. pi-approx; App. A):
@@ -365,6 +395,22 @@ tnmc_status tnmc_batch_init_chains(tnmc_batch* plan, uint64_t seed, int8_t* chai
 tnmc_status tnmc_mh_batched(tnmc_batch* plan, const int8_t* prop_spins, const double* prop_logq,
                             const double* prop_energy, int8_t* chain_spins, double* chain_logq,
                             double* chain_energy, uint8_t* accepted, int64_t* n_accepted, void* stream);
+
+/*
+ * tnmc_metropolis for every chain of every instance in one launch, then the forced log q
+ * and energy of the whole chain arena in one persistent launch.  At plan step k chain c of
+ * instance i has chain id (uint32)(i * chains + c) and runs sweeps k * sweeps .. +sweeps-1
+ * with the plan's seed: per instance identical to tnmc_metropolis(env_i, plan precision,
+ * chains, ..., seed, i * chains, k * sweeps, sweeps).  Allocates nothing (capturable).
+ */
+tnmc_status tnmc_metropolis_batched(tnmc_batch* plan, int8_t* chain_spins, double* chain_logq, double* chain_energy,
+                                    int sweeps, void* stream);
+
+/*
+ * tnmc_link_overlap of every instance's replica pairs: overlap [n][chains / 2] (device
+ * double), instance-major; chains must be even.
+ */
+tnmc_status tnmc_link_overlap_batched(tnmc_batch* plan, const int8_t* chain_spins, double* overlap, void* stream);
 
 #ifdef __cplusplus
 }

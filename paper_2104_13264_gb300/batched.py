@@ -94,7 +94,7 @@ class BatchRunner:
     """
 
     def __init__(self, envs, B, chains=1, precision="f32", tile=None, order=None, seed=0, tune=True,
-                 cache_path=CACHE_PATH, log=None):
+                 cache_path=CACHE_PATH, log=None, sweeps=0):
         import torch
         if tile is None or order is None:
             if tune:
@@ -110,12 +110,30 @@ class BatchRunner:
         self.accepted = torch.zeros(inf["proposal_rows"], dtype=torch.uint8, device="cuda")
         self.n_accepted = torch.zeros(self.plan.n, dtype=torch.int64, device="cuda")
         self.plan.set_step(seed, 0)
+        self.sweeps = int(sweeps)
         self.graph = None
 
     def _launch(self):
         self.plan.sample(self.prop)
         self.plan.mh(self.prop, self.chain, self.accepted, self.n_accepted)
+        if self.sweeps:
+            # single-spin-flip Metropolis sweeps between proposals (Sec. 3, Table hb)
+            self.plan.metropolis(self.chain, self.sweeps)
         self.plan.advance()
+
+    def delta(self):
+        """The equilibration diagnostic of Sec. 3 (eq. Delta) over the plan's instances:
+        the mean over instances of (1/|V|)(<H> + beta (|E| - sum <s_i s_j>^2)), with <H> the
+        chains' mean energy and the link overlap averaged over replica pairs (2k, 2k+1).
+        It vanishes at equilibrium on average over Gaussian disorder."""
+        import torch
+        q = self.plan.link_overlap(self.chain[0]).mean(dim=1)
+        E = self.chain[2].view(self.plan.n, self.plan.chains).mean(dim=1)
+        dims = torch.tensor([[e.Lx, e.Ly, e.beta] for e in self.plan.envs], dtype=torch.float64, device=E.device)
+        Lx, Ly, beta = dims[:, 0], dims[:, 1], dims[:, 2]
+        nb = Ly * (Lx - 1) + (Ly - 1) * Lx
+        d = (E + beta * (nb - q)) / (Lx * Ly)
+        return float(d.mean().item()), d
 
     def step_eager(self):
         self._launch()

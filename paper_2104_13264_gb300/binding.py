@@ -75,6 +75,10 @@ SIGNATURES = {
     "tnmc_batch_init_chains": ([_P, _U64, _P, _P, _P, _P], _INT),
     "tnmc_mh_batched": ([_P, _P, _P, _P, _P, _P, _P, _P, _P, _P], _INT),
     "tnmc_set_allocator": ([_P, _P, _P], _INT),
+    "tnmc_metropolis": ([_P, _INT, _I64, _P, _P, _P, _U64, _U64, _U64, _INT, _P], _INT),
+    "tnmc_link_overlap": ([_P, _I64, _P, _P, _P], _INT),
+    "tnmc_metropolis_batched": ([_P, _P, _P, _P, _INT, _P], _INT),
+    "tnmc_link_overlap_batched": ([_P, _P, _P, _P], _INT),
 }
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -258,6 +262,24 @@ def mh_step(env, C, T, prop, chain, seed=0, step_offset=0, accepted=None, n_acce
     return accepted
 
 
+def metropolis(env, chain, seed=0, chain_offset=0, sweep_offset=0, sweeps=1, precision="f64", stream=None):
+    """Checkerboard Metropolis sweeps of chain = (spins, logq, energy) in place; the chains'
+    log q and energy are recomputed afterwards."""
+    cs, clq, cE = chain
+    _check(lib().tnmc_metropolis(env.handle, PRECISIONS[precision], cs.shape[0], _ptr(cs), _ptr(clq), _ptr(cE), seed,
+                                 chain_offset, sweep_offset, int(sweeps), _stream(stream)))
+    return chain
+
+
+def link_overlap(env, chain_spins, stream=None):
+    """Link overlap of the replica pairs (2k, 2k+1): float64 cuda tensor [C / 2]."""
+    import torch
+    C = chain_spins.shape[0]
+    out = torch.empty(C // 2, dtype=torch.float64, device=chain_spins.device)
+    _check(lib().tnmc_link_overlap(env.handle, C, _ptr(chain_spins), _ptr(out), _stream(stream)))
+    return out
+
+
 def param_count(env):
     inf = env.info()
     return env.Ly * env.Lx * inf["pad"] * 2 * inf["pad"]
@@ -421,6 +443,20 @@ class Batch:
         _check(lib().tnmc_mh_batched(self._h, _ptr(ps), _ptr(plq), _ptr(pE), _ptr(cs), _ptr(clq), _ptr(cE),
                                      _ptr(accepted), _ptr(n_accepted), _stream(stream)))
         return accepted
+
+    def metropolis(self, chain, sweeps=1, stream=None):
+        """Metropolis sweeps of every chain (plan seed and step), then their log q and energy."""
+        cs, clq, cE = chain
+        _check(lib().tnmc_metropolis_batched(self._h, _ptr(cs), _ptr(clq), _ptr(cE), int(sweeps), _stream(stream)))
+        return chain
+
+    def link_overlap(self, chain_spins, out=None, stream=None):
+        """Link overlaps of every instance's replica pairs: float64 cuda tensor [n, chains / 2]."""
+        import torch
+        if out is None:
+            out = torch.empty((self.n, self.chains // 2), dtype=torch.float64, device=chain_spins.device)
+        _check(lib().tnmc_link_overlap_batched(self._h, _ptr(chain_spins), _ptr(out), _stream(stream)))
+        return out
 
     def free(self):
         if self._h is not None and self._h.value:

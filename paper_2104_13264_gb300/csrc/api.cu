@@ -433,6 +433,35 @@ tnmc_status tnmc_mh_step(const tnmc_env* env, int64_t C, int64_t T, const int8_t
                         step_offset, accepted, n_accepted, static_cast<cudaStream_t>(stream));
 }
 
+tnmc_status tnmc_metropolis(const tnmc_env* env, int precision, int64_t C, int8_t* chain_spins, double* chain_logq,
+                            double* chain_energy, uint64_t seed, uint64_t chain_offset, uint64_t sweep_offset,
+                            int sweeps, void* stream) {
+  g_err[0] = 0;
+  CHECK_ARG(env, "env must be non-null");
+  CHECK_ARG(C >= 0 && C < ((int64_t)1 << 32), "C out of range");
+  CHECK_ARG(sweeps >= 0, "sweeps must be >= 0");
+  CHECK_ARG(C == 0 || (chain_spins && chain_logq && chain_energy), "chain arrays must be non-null");
+  CHECK_ARG((size_t)env->d.Lx * env->d.Ly <= 200 * 1024, "a chain of %d sites does not fit in shared memory",
+            env->d.Lx * env->d.Ly);
+  tnmc_status st = check_precision(env, precision);
+  if (st != TNMC_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  st = tnmc_launch_metropolis(env, C, chain_spins, seed, chain_offset, sweep_offset, sweeps, s);
+  if (st != TNMC_OK) return st;
+  // the chain states changed: their log q and energy, as tnmc_logq computes them
+  return tnmc_launch_sample(env, precision, C, 0, 0, chain_spins, nullptr, chain_logq, chain_energy, nullptr, s);
+}
+
+tnmc_status tnmc_link_overlap(const tnmc_env* env, int64_t C, const int8_t* chain_spins, double* overlap,
+                              void* stream) {
+  g_err[0] = 0;
+  CHECK_ARG(env, "env must be non-null");
+  CHECK_ARG(C >= 0 && C % 2 == 0, "C = %lld must be even (replica pairs)", (long long)C);
+  CHECK_ARG(C == 0 || (chain_spins && overlap), "chain_spins and overlap must be non-null");
+  return tnmc_launch_link_overlap(env->d.Lx, env->d.Ly, C / 2, chain_spins, overlap,
+                                  static_cast<cudaStream_t>(stream));
+}
+
 tnmc_status tnmc_logq_backward(const tnmc_env* env, int64_t B, const int8_t* spins, const float* weights,
                                float* grad, void* stream) {
   g_err[0] = 0;

@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "metropolis_kernel.cuh"
 #include "sample_simt_kernel.cuh"
 
 namespace tnmc {
@@ -146,6 +147,40 @@ __global__ void init_batched_kernel(const MhInst* __restrict__ inst, int64_t tot
   }
 }
 
+// Metropolis sweeps of every chain (one CTA per chain at a time): chain c of instance i
+// has id i C + c and, at plan step k, runs sweeps k * sweeps .. k * sweeps + sweeps - 1.
+__global__ void metropolis_batched_kernel(const MetroInst* __restrict__ inst, int64_t total, int64_t C,
+                                          const uint64_t* params, int sweeps, int8_t* chains) {
+  extern __shared__ int8_t sm[];
+  const uint64_t seed = params[0];
+  const uint32_t sweep0 = (uint32_t)(params[1] * (uint64_t)sweeps);
+  for (int64_t g = blockIdx.x; g < total; g += gridDim.x) {
+    const int64_t i = g / C, c = g % C;
+    const MetroInst I = inst[i];
+    const int n = I.Lx * I.Ly;
+    int8_t* dst = chains + I.chain_spin + c * n;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) sm[k] = dst[k];
+    __syncthreads();
+    metropolis_chain(I, sm, seed, (uint32_t)g, sweep0, sweeps);
+    for (int k = threadIdx.x; k < n; k += blockDim.x) dst[k] = sm[k];
+    __syncthreads();
+  }
+}
+
+// Link overlap of replica pair k of instance i (output row i * half + k).
+__global__ void link_overlap_batched_kernel(const MetroInst* __restrict__ inst, int64_t total, int64_t half,
+                                            const int8_t* chains, double* out) {
+  __shared__ long long red[32];
+  for (int64_t g = blockIdx.x; g < total; g += gridDim.x) {
+    const int64_t i = g / half, k = g % half;
+    const MetroInst I = inst[i];
+    const int64_t n = (int64_t)I.Lx * I.Ly;
+    const int8_t* a = chains + I.chain_spin + 2 * k * n;
+    const double q = link_overlap_pair(I.Lx, I.Ly, a, a + n, red);
+    if (threadIdx.x == 0) out[g] = q;
+  }
+}
+
 __global__ void set_params_kernel(uint64_t* params, uint64_t seed, uint64_t step) {
   params[0] = seed;
   params[1] = step;
@@ -193,6 +228,8 @@ struct tnmc_batch {
   int2* d_items_prop = nullptr;
   int2* d_items_chain = nullptr;
   tnmc::MhInst* d_mh = nullptr;
+  tnmc::MetroInst* d_metro = nullptr;
+  int max_sites = 0;
   unsigned int* d_counter = nullptr;
   uint64_t* d_params = nullptr;
   int64_t* d_last = nullptr;
@@ -351,6 +388,7 @@ tnmc_status tnmc_batch_create(int n, tnmc_env* const* envs, const int64_t* B, in
   size_t max_stack = 1;
   std::vector<double> cost(n);
   std::vector<tnmc::MhInst> mh(n);
+  std::vector<tnmc::MetroInst> metro(n);
   for (int i = 0; i < n; ++i) {
     const DeviceEnv& d = envs[i]->d;
     const int64_t ns = (int64_t)d.Lx * d.Ly;
@@ -369,6 +407,8 @@ tnmc_status tnmc_batch_create(int n, tnmc_env* const* envs, const int64_t* B, in
     max_stack = std::max(max_stack, (size_t)(d.Lx + 1) * d.P * tile);
     cost[i] = instance_cost(d);
     mh[i] = tnmc::MhInst{d.beta, ns, B[i] / chains, p->prop_row[i], p->prop_spin[i], p->chain_spin[i]};
+    metro[i] = tnmc::MetroInst{d.Jh, d.Jv, d.h, d.beta, d.Lx, d.Ly, p->chain_spin[i]};
+    p->max_sites = std::max(p->max_sites, (int)ns);
   }
   if (p->items_prop >= (1ll << 31) || p->items_chain >= (1ll << 31)) {
     delete p;
@@ -410,6 +450,7 @@ tnmc_status tnmc_batch_create(int n, tnmc_env* const* envs, const int64_t* B, in
   const size_t o_pr = take(n * 8), o_ps = take(n * 8), o_cr = take(n * 8), o_cs = take(n * 8);
   const size_t o_ip = take(ip.size() * sizeof(int2)), o_ic = take(ic.size() * sizeof(int2));
   const size_t o_mh = take(n * sizeof(tnmc::MhInst)), o_cnt = take(2 * sizeof(unsigned int));
+  const size_t o_metro = take(n * sizeof(tnmc::MetroInst));
   const size_t o_par = take(2 * sizeof(uint64_t)), o_last = take((size_t)p->chain_rows * 8);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   p->alloc = current_allocator();
@@ -434,6 +475,7 @@ tnmc_status tnmc_batch_create(int n, tnmc_env* const* envs, const int64_t* B, in
   p->d_items_prop = reinterpret_cast<int2*>(base + o_ip);
   p->d_items_chain = reinterpret_cast<int2*>(base + o_ic);
   p->d_mh = reinterpret_cast<tnmc::MhInst*>(base + o_mh);
+  p->d_metro = reinterpret_cast<tnmc::MetroInst*>(base + o_metro);
   p->d_counter = reinterpret_cast<unsigned int*>(base + o_cnt);
   p->d_params = reinterpret_cast<uint64_t*>(base + o_par);
   p->d_last = reinterpret_cast<int64_t*>(base + o_last);
@@ -466,6 +508,7 @@ tnmc_status tnmc_batch_create(int n, tnmc_env* const* envs, const int64_t* B, in
   up(p->d_items_prop, ip.data(), ip.size() * sizeof(int2));
   up(p->d_items_chain, ic.data(), ic.size() * sizeof(int2));
   up(p->d_mh, mh.data(), n * sizeof(tnmc::MhInst));
+  up(p->d_metro, metro.data(), n * sizeof(tnmc::MetroInst));
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
     tnmc_set_error("batch plan upload failed: %s", cudaGetErrorString(e));
@@ -571,6 +614,40 @@ tnmc_status tnmc_mh_batched(tnmc_batch* p, const int8_t* prop_spins, const doubl
   TNMC_CUDA_TRY(cudaGetLastError());
   mh_batched_copy_kernel<<<(unsigned)std::min<int64_t>(total, 65535), 256, 0, s>>>(p->d_mh, total, p->chains,
                                                                                   p->d_last, prop_spins, chain_spins);
+  TNMC_CUDA_TRY(cudaGetLastError());
+  return TNMC_OK;
+}
+
+tnmc_status tnmc_metropolis_batched(tnmc_batch* p, int8_t* chain_spins, double* chain_logq, double* chain_energy,
+                                    int sweeps, void* stream) {
+  using namespace tnmc;
+  CHECK_ARG(p, "plan must be non-null");
+  CHECK_ARG(sweeps >= 0, "sweeps must be >= 0");
+  CHECK_ARG(chain_spins && chain_logq && chain_energy, "chain arrays must be non-null");
+  CHECK_ARG(p->max_sites <= 200 * 1024, "a chain of %d sites does not fit in shared memory", p->max_sites);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int64_t total = p->chain_rows;
+  if (sweeps > 0) {
+    const size_t smem = (size_t)p->max_sites;
+    if (smem > 48 * 1024)
+      TNMC_CUDA_TRY(cudaFuncSetAttribute(metropolis_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    metropolis_batched_kernel<<<(unsigned)std::min<int64_t>(total, 65535), 256, smem, s>>>(
+        p->d_metro, total, p->chains, p->d_params, sweeps, chain_spins);
+    TNMC_CUDA_TRY(cudaGetLastError());
+  }
+  return dispatch_batched(p, true, chain_spins, nullptr, chain_logq, chain_energy, nullptr, s);
+}
+
+tnmc_status tnmc_link_overlap_batched(tnmc_batch* p, const int8_t* chain_spins, double* overlap, void* stream) {
+  using namespace tnmc;
+  CHECK_ARG(p, "plan must be non-null");
+  CHECK_ARG(p->chains % 2 == 0, "chains = %lld must be even (replica pairs)", (long long)p->chains);
+  CHECK_ARG(chain_spins && overlap, "chain_spins and overlap must be non-null");
+  const int64_t half = p->chains / 2;
+  const int64_t total = (int64_t)p->n * half;
+  if (total == 0) return TNMC_OK;
+  link_overlap_batched_kernel<<<(unsigned)std::min<int64_t>(total, 65535), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+      p->d_metro, total, half, chain_spins, overlap);
   TNMC_CUDA_TRY(cudaGetLastError());
   return TNMC_OK;
 }

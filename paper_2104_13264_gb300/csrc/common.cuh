@@ -196,3 +196,7 @@ tnmc_status tnmc_launch_mh(const tnmc_env* env, int64_t C, int64_t T, const int8
                            cudaStream_t stream);
 tnmc_status tnmc_launch_init_bits(const tnmc_env* env, int64_t C, uint64_t seed, int8_t* spins,
                                   cudaStream_t stream);
+tnmc_status tnmc_launch_metropolis(const tnmc_env* env, int64_t C, int8_t* chains, uint64_t seed,
+                                   uint64_t chain_offset, uint64_t sweep_offset, int sweeps, cudaStream_t stream);
+tnmc_status tnmc_launch_link_overlap(int Lx, int Ly, int64_t pairs, const int8_t* chains, double* out,
+                                     cudaStream_t stream);
