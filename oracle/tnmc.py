@@ -527,3 +527,102 @@ def delta_from_chains(beta, Lx, Ly, chain_spins, chain_energy):
     sp = np.asarray(chain_spins)
     q = link_overlap(None, None, sp[0::2], sp[1::2])
     return delta_instance(beta, Lx, Ly, float(np.mean(chain_energy)), float(np.mean(q)))
+
+
+# ---- arbitrary boundary conditions by frozen lines (App. B) ----
+
+def energy_periodic(Jh, Jv, h, spins, px, py):
+    """H of eq. ising on an Ly x Lx lattice that may close in x (px) and/or y (py):
+    Jh [Ly, Lx] bond (r, c)-(r, c+1 mod Lx) (the last column used only when px),
+    Jv [Ly, Lx] bond (r, c)-(r+1 mod Ly, c) (the last row used only when py)."""
+    s = np.asarray(spins, dtype=np.float64)
+    E = -(np.asarray(h)[None] * s).sum(axis=(1, 2))
+    Lx = s.shape[2]
+    Ly = s.shape[1]
+    Jh = np.asarray(Jh, dtype=np.float64)
+    Jv = np.asarray(Jv, dtype=np.float64)
+    E -= (Jh[None, :, :Lx - 1] * s[:, :, :-1] * s[:, :, 1:]).sum(axis=(1, 2))
+    if px:
+        E -= (Jh[None, :, Lx - 1] * s[:, :, -1] * s[:, :, 0]).sum(axis=1)
+    E -= (Jv[None, :Ly - 1, :] * s[:, :-1, :] * s[:, 1:, :]).sum(axis=(1, 2))
+    if py:
+        E -= (Jv[None, Ly - 1, :] * s[:, -1, :] * s[:, 0, :]).sum(axis=1)
+    return E
+
+
+def frozen_cut(Jh, Jv, h, spins, kr, kc, px, py):
+    """The open-boundary instance left when column kc (if px) and row kr (if py) are frozen
+    (App. B): the free rows are kr+1, ..., kr-1 (mod Ly) when py (all rows otherwise), the
+    free columns likewise, in that order.  Bonds between free sites keep their couplings;
+    a bond from a free site to a frozen one becomes a field J s_frozen on the free site.
+    Returns (rows, cols, Jh_eff [ly, lx-1], Jv_eff [ly-1, lx], h_eff [C, ly, lx])."""
+    s = np.asarray(spins, dtype=np.float64)
+    C, Ly, Lx = s.shape
+    rows = [(kr + 1 + i) % Ly for i in range(Ly - 1)] if py else list(range(Ly))
+    cols = [(kc + 1 + j) % Lx for j in range(Lx - 1)] if px else list(range(Lx))
+    Jh = np.asarray(Jh, dtype=np.float64)
+    Jv = np.asarray(Jv, dtype=np.float64)
+    h = np.asarray(h, dtype=np.float64)
+    ly, lx = len(rows), len(cols)
+    Jh_e = np.array([[Jh[r, cols[j]] for j in range(lx - 1)] for r in rows]).reshape(ly, max(lx - 1, 0))
+    Jv_e = np.array([[Jv[rows[i], c] for c in cols] for i in range(ly - 1)]).reshape(max(ly - 1, 0), lx)
+    h_e = np.broadcast_to(h[np.ix_(rows, cols)], (C, ly, lx)).copy()
+    frozen_c = {kc} if px else set()
+    frozen_r = {kr} if py else set()
+    for i, r in enumerate(rows):
+        for j, c in enumerate(cols):
+            # the four neighbours of (r, c) on the closed lattice; bonds to frozen sites
+            nbrs = []
+            if px or c + 1 < Lx:
+                nbrs.append((r, (c + 1) % Lx, Jh[r, c]))
+            if px or c > 0:
+                nbrs.append((r, (c - 1) % Lx, Jh[r, (c - 1) % Lx]))
+            if py or r + 1 < Ly:
+                nbrs.append(((r + 1) % Ly, c, Jv[r, c]))
+            if py or r > 0:
+                nbrs.append(((r - 1) % Ly, c, Jv[(r - 1) % Ly, c]))
+            for rn, cn, J in nbrs:
+                if rn in frozen_r or cn in frozen_c:
+                    h_e[:, i, j] += J * s[:, rn, cn]
+    return rows, cols, Jh_e, Jv_e, h_e
+
+
+def frozen_line_step(Jh, Jv, h, beta, chi, chains, kr, kc, px, py, seed, step, T):
+    """One move of Markov chains on a closed lattice (App. B): freeze the line(s), build the
+    environment of each chain's open instance (its frozen spins enter as fields), draw T
+    proposals of the free spins from it and run the MH scan against the chain's current
+    free spins (whose log q is evaluated under the same environment).  The frozen spins
+    do not change, so the free spins' conditional law pi(free | frozen) is the Boltzmann
+    weight of the open instance and the move keeps pi invariant.
+
+    Chain i is instance i: its proposals use sample indices (i << 40) + step T + t and its
+    MH uniforms the step offsets (i << 40) + step T (chain 0 of the instance).  Returns
+    (new chain spins [C, Ly, Lx], accepted [C, T])."""
+    sp = np.array(chains, dtype=np.int8, copy=True)
+    C = sp.shape[0]
+    rows, cols, Jh_e, Jv_e, h_e = frozen_cut(Jh, Jv, h, sp, kr, kc, px, py)
+    acc = np.zeros((C, T), dtype=bool)
+    # chains with the same frozen spins have the same open instance, hence one environment
+    groups = {}
+    for i in range(C):
+        groups.setdefault(h_e[i].tobytes(), []).append(i)
+    for members in groups.values():
+        idx = np.array(members)
+        env = build_env(Jh_e, Jv_e, h_e[idx[0]], beta, chi)
+        off = (idx.astype(np.uint64) << np.uint64(40)) + np.uint64(step * T)      # per chain
+        psp, plq, pE, _ = sample(env, idx.size * T, seed=seed,
+                                 samples=(off[:, None] + np.arange(T, dtype=np.uint64)[None, :]).ravel())
+        cur = sp[idx][:, rows][:, :, cols]
+        _, lq, E, _ = logq(env, cur)
+        # the MH scan of each chain over its T proposals (chain 0 of its own instance)
+        for j in range(T):
+            t = np.arange(idx.size) * T + j
+            u = philox.mh_uniform(seed, off + np.uint64(j), 0)
+            a = mh_accept(beta, plq[t], pE[t], lq, E, u)
+            acc[idx, j] = a
+            lq = np.where(a, plq[t], lq)
+            E = np.where(a, pE[t], E)
+            cur = np.where(a[:, None, None], psp[t], cur)
+        for k, i in enumerate(idx):
+            sp[i][np.ix_(rows, cols)] = cur[k]
+    return sp, acc
