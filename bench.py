@@ -21,6 +21,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -34,7 +36,17 @@ CONFIGS = {
     "c5": ("config5", 1 << 20, 1024, "bf16", "256x256 ferromagnet, beta=0.4407, chi=64, B=2^20"),
     "c5p": ("config5_strip", 65536, 64, "bf16", "16x256 ferromagnet strip (Lx, beta, chi of the 256x256 case), "
                                                "B=65536: profiling case of the sampler kernels"),
+    "c3p": ("gaussian_ea_torus_batch", 16, 16, "f64", "32 Gaussian EA disorder samples on 32x32 tori, T=0.212, chi=16, "
+                                                       "16 chains each: frozen-line TNMH moves (random cuts), Delta diagnostic"),
+    "c3d": ("gaussian_ea_batch", 32, 32, "f64", "256 Gaussian EA instances 32x32, T=0.212, chi=16, 32 chains each: "
+                                               "TNMH move + one Metropolis sweep per iteration, Delta diagnostic"),
 }
+
+# the paper's Table hb row for TNMH + Metropolis: iterations to reach each Delta threshold
+# (10^4 disorders, 30 chains; hardware unstated) -- context for the measured counts
+TABLE_HB = {"thresholds": [0.25, 0.15, 0.05, 0.025], "tnmh_plus_metropolis": [3, 3, 5, 5]}
+# Table hbpbc (periodic boundaries, frozen-line moves): TNMH iterations (upper bounds)
+TABLE_HBPBC = {"thresholds": [0.25, 0.15, 0.05, 0.025], "tnmh": [14, 21, 40, 56]}
 
 
 def algorithmic_flops(inst):
@@ -501,6 +513,138 @@ def run_batched(args):
         pg.destroy_process_group()
 
 
+def run_equilibration(args):
+    """The paper's equilibration test (Sec. 3, Table hb) on the batched form: every
+    iteration draws one proposal per chain (one persistent launch), runs the MH scan,
+    one checkerboard Metropolis sweep of every chain and the forced log q of the new
+    chain states, all replayed from one captured CUDA graph.  Reports iterations/s and
+    the Delta diagnostic (eq. Delta) after each iteration of a fresh run."""
+    import torch
+    from paper_2104_13264_gb300 import batched
+    from paper_2104_13264_gb300 import binding as Bd
+    from paper_2104_13264_gb300 import instances
+
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    fac, Bdef, Cdef, pdef, desc = CONFIGS["c3d"]
+    insts = instances.gaussian_ea_batch()
+    C = args.chains or Cdef
+    T = max(1, (args.batch or Bdef) // C)
+    prec = args.precision or pdef
+    stream = torch.cuda.current_stream()
+    t0 = time.time()
+    envs = Bd.build_envs_batched(insts, precisions=tuple(sorted({"f64", prec})))
+    statuses = [e.status() for e in envs]
+    env_build_s = time.time() - t0
+    run = batched.BatchRunner(envs, C * T, chains=C, precision=prec, tile=64, order="cost", tune=False,
+                              seed=args.seed + 7919 * rank, sweeps=1)
+    run.capture()
+    # Delta after each iteration of a fresh run (the first graph replay is iteration 1)
+    deltas = [run.delta()[0]]
+    for _ in range(args.iters):
+        run.step()
+        deltas.append(run.delta()[0])
+    reached = {}
+    for thr in TABLE_HB["thresholds"]:
+        hit = next((k for k, d in enumerate(deltas) if abs(d) < thr), None)
+        reached[str(thr)] = hit
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        run.step()
+    torch.cuda.synchronize()
+    run.n_accepted.zero_()
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        run.step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = e0.elapsed_time(e1)
+    props = len(insts) * C * T
+    acc = int(run.n_accepted.sum().item()) / (props * args.steps)
+    if rank != 0:
+        return
+    # algorithmic work per iteration: the proposals and the forced evaluation of the chains
+    flops = sum(algorithmic_flops(i) for i in insts) * C * (T + 1)
+    it_s = args.steps / (total_ms / 1e3)
+    peaks, _ = load_peaks()
+    smmax = float(peaks.get("sm_max_mhz", 2070.0))
+    if prec == "f32":
+        peak, psrc = 152 * 128 * 2 * smmax * 1e6 / 1e12, "FP32 FFMA nominal: 152 SM x 128 lanes x 2 x %.0f MHz" % smmax
+    else:
+        peak, psrc = 1.25, "FP64 nominal 1.25 TFLOP/s"
+    achieved = flops * it_s / 1e12
+    line = {
+        "metric": "TNMH + Metropolis iterations/s (%s)" % desc, "value": round(it_s, 3), "unit": "iterations/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": prec, "data": "synthetic (seeded Gaussian couplings)",
+        "config": {"workload": "c3d", "description": desc, "instances": len(insts), "L": 32, "T": 0.212, "chi": 16,
+                   "chains_per_instance": C, "proposals_per_chain_per_iteration": T, "metropolis_sweeps": 1,
+                   "precision": prec, "l2": "working set < L2 (graph replays back to back)"},
+        "acceptance": round(acc, 5), "env_build_s": round(env_build_s, 3),
+        "device_status_nonzero": sum(1 for s_ in statuses if s_),
+        "delta_trajectory": [round(d, 5) for d in deltas],
+        "iterations_to_delta": reached, "paper_table_hb": TABLE_HB,
+        "roofline": {"bound": "alu", "unit": "TFLOP/s", "achieved": round(achieved, 4), "peak": peak,
+                     "frac": round(achieved / peak, 5), "traffic": None, "kernel": "whole iteration",
+                     "flop_per_iteration": flops, "peak_source": psrc},
+        "cpu_baseline": None, "e2e": None, "gpu_launches": 6 * args.steps, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_frozen(args):
+    """Closed lattices by frozen lines (App. B, Table hbpbc): every move freezes a random
+    row and column of each torus, builds one environment per chain for the open lattice
+    left (one batched builder launch), draws the proposals of the free spins (one
+    persistent launch), evaluates the current free spins and runs the MH scan.  Reports
+    moves/s (wall clock: the host assembles the open instances) and Delta per move."""
+    import torch
+    from paper_2104_13264_gb300 import frozen, instances
+
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    fac, Bdef, Cdef, pdef, desc = CONFIGS["c3p"]
+    Jh, Jv, h, beta = instances.gaussian_ea_torus_batch()
+    C = args.chains or Cdef
+    prec = args.precision or pdef
+    D, L = Jh.shape[0], Jh.shape[1]
+    start = np.random.default_rng([args.seed, 19]).choice([-1, 1], size=(D, C, L, L)).astype(np.int8)
+    ch = frozen.FrozenLineChains(Jh, Jv, h, beta, 16, start, precision=prec, proposals=1, seed=args.seed + 7919 * rank)
+    deltas = [ch.delta()[0]]
+    acc, walls = [], []
+    for _ in range(args.iters):
+        torch.cuda.synchronize()
+        t0 = time.time()
+        a = ch.step()
+        torch.cuda.synchronize()
+        walls.append(time.time() - t0)
+        acc.append(a.float().mean().item())
+        deltas.append(ch.delta()[0])
+    if rank != 0:
+        return
+    reached = {str(t): next((k for k, d in enumerate(deltas) if abs(d) < t), None) for t in TABLE_HBPBC["thresholds"]}
+    timed = walls[args.warmup:] or walls
+    per = statistics.mean(timed)
+    line = {
+        "metric": "frozen-line TNMH moves/s (%s)" % desc, "value": round(1.0 / per, 4), "unit": "moves/s",
+        "n_gpus": world, "steps": len(timed), "warmup": min(args.warmup, len(walls)),
+        "ms_per_step": round(per * 1e3, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": prec, "data": "synthetic (seeded Gaussian couplings)",
+        "config": {"workload": "c3p", "description": desc, "disorders": D, "L": L, "T": 0.212, "chi": 16,
+                   "chains_per_disorder": C, "proposals_per_chain_per_move": 1, "cuts": "random row and column",
+                   "environments_per_move": D * C, "timing": "wall clock per move (host cut + GPU work)"},
+        "acceptance": round(float(np.mean(acc)), 5), "delta_trajectory": [round(d, 5) for d in deltas],
+        "iterations_to_delta": reached, "paper_table_hbpbc": TABLE_HBPBC,
+        "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def plain_batched_f64(Bd, envs, insts, B, C, args, stream):
     """The plain FP64 form of the batched workload: one tnmc_sample + tnmc_mh_step per
     instance, FP64, no graph, default tiles."""
@@ -574,7 +718,7 @@ def _oracle_workload(config, n_rows_cap):
     from paper_2104_13264_gb300 import instances
     fac = CONFIGS[config][0]
     inst = getattr(instances, fac)()
-    if config == "c3":
+    if config in ("c3", "c3d"):
         # a cost-weighted sample: one of the largest instances (L = 64, chi = 32) stands for
         # the mean by the ratio of algorithmic work, applied by the caller
         insts = inst
@@ -798,6 +942,7 @@ def main():
     ap.add_argument("--cpu-batch", type=int, default=0)
     ap.add_argument("--plain-batch", type=int, default=2 * 152 * 64)   # one full wave of the FP64 kernel
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--iters", type=int, default=30, help="iterations of the Delta trajectory (c3d)")
     ap.add_argument("--tune-steps", type=int, default=0,
                     help="tuning steps of the FP32 tensors before the timed sampling (the 64x64 Villain case uses 50)")
     args = ap.parse_args()
@@ -805,6 +950,10 @@ def main():
         run_reference(args)
     elif args.config == "c3":
         run_batched(args)
+    elif args.config == "c3d":
+        run_equilibration(args)
+    elif args.config == "c3p":
+        run_frozen(args)
     else:
         run_tnmc(args)
 

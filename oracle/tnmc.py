@@ -587,7 +587,7 @@ def frozen_cut(Jh, Jv, h, spins, kr, kc, px, py):
     return rows, cols, Jh_e, Jv_e, h_e
 
 
-def frozen_line_step(Jh, Jv, h, beta, chi, chains, kr, kc, px, py, seed, step, T):
+def frozen_line_step(Jh, Jv, h, beta, chi, chains, kr, kc, px, py, seed, step, T, instance_offset=0):
     """One move of Markov chains on a closed lattice (App. B): freeze the line(s), build the
     environment of each chain's open instance (its frozen spins enter as fields), draw T
     proposals of the free spins from it and run the MH scan against the chain's current
@@ -595,8 +595,9 @@ def frozen_line_step(Jh, Jv, h, beta, chi, chains, kr, kc, px, py, seed, step, T
     do not change, so the free spins' conditional law pi(free | frozen) is the Boltzmann
     weight of the open instance and the move keeps pi invariant.
 
-    Chain i is instance i: its proposals use sample indices (i << 40) + step T + t and its
-    MH uniforms the step offsets (i << 40) + step T (chain 0 of the instance).  Returns
+    Chain i is instance j = instance_offset + i: its proposals use sample indices
+    (j << 40) + step T + t and its MH uniforms the step offsets (j << 40) + step T (chain 0
+    of the instance).  Returns
     (new chain spins [C, Ly, Lx], accepted [C, T])."""
     sp = np.array(chains, dtype=np.int8, copy=True)
     C = sp.shape[0]
@@ -609,7 +610,7 @@ def frozen_line_step(Jh, Jv, h, beta, chi, chains, kr, kc, px, py, seed, step, T
     for members in groups.values():
         idx = np.array(members)
         env = build_env(Jh_e, Jv_e, h_e[idx[0]], beta, chi)
-        off = (idx.astype(np.uint64) << np.uint64(40)) + np.uint64(step * T)      # per chain
+        off = ((idx + instance_offset).astype(np.uint64) << np.uint64(40)) + np.uint64(step * T)   # per chain
         psp, plq, pE, _ = sample(env, idx.size * T, seed=seed,
                                  samples=(off[:, None] + np.arange(T, dtype=np.uint64)[None, :]).ravel())
         cur = sp[idx][:, rows][:, :, cols]

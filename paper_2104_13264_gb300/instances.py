@@ -116,6 +116,22 @@ def config4():
     return villain(64, 64, 1.5, 32)
 
 
+def gaussian_ea_batch(n=256, L=32, T=0.212, chi=16, seed=0):
+    """n Gaussian EA instances on L x L open lattices at temperature T: the setting of the
+    paper's equilibration test (Sec. 3, Fig. hb b, Table hb: 32 x 32, T = 0.212, D = 16)."""
+    return [ea_gauss(L, L, 1.0 / T, chi, seed=seed * 100003 + 7919 + i) for i in range(n)]
+
+
+def gaussian_ea_torus_batch(n=32, L=32, T=0.212, seed=0):
+    """n Gaussian EA disorder samples on L x L tori (periodic in both directions) at
+    temperature T: couplings (Jh, Jv) as [n, L, L] stacks (bond (r, c)-(r, c+1 mod L) and
+    (r, c)-(r+1 mod L, c)), N(0, 1) drawn in float32 and widened; h = 0; beta = 1 / T."""
+    rng = np.random.default_rng([seed, 17])
+    Jh = rng.standard_normal((n, L, L)).astype(np.float32).astype(np.float64)
+    Jv = rng.standard_normal((n, L, L)).astype(np.float32).astype(np.float64)
+    return Jh, Jv, np.zeros((n, L, L)), 1.0 / T
+
+
 def config5():
     """256x256 ferromagnet at beta = 0.4407, chi = 64, B = 2^20."""
     return ferromagnet(256, 256, 0.4407, 64)

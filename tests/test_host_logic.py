@@ -46,3 +46,23 @@ def test_reference_arm_prints_contract_line():
     assert line["config"]["workload"] == "c1"
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_open_instances_match_the_oracle_cut():
+    """The frozen-line driver's open instances (couplings and fields from the frozen spins)
+    are the oracle's, for the three closed geometries and several cuts."""
+    import numpy as np
+
+    from oracle import tnmc
+    from paper_2104_13264_gb300 import frozen
+    r = np.random.default_rng(4)
+    for Ly, Lx in ((5, 6), (2, 3), (3, 2)):
+        Jh, Jv, h = r.standard_normal((Ly, Lx)), r.standard_normal((Ly, Lx)), r.standard_normal((Ly, Lx))
+        sp = r.choice([-1, 1], size=(7, Ly, Lx)).astype(np.int8)
+        for px, py in ((True, True), (True, False), (False, True)):
+            for kr, kc in ((0, 0), (Ly - 1, 1), (1, Lx - 1)):
+                a = frozen.open_instances(Jh, Jv, h, sp, kr, kc, px, py)
+                b = tnmc.frozen_cut(Jh, Jv, h, sp, kr, kc, px, py)
+                assert list(a[0]) == list(b[0]) and list(a[1]) == list(b[1])
+                for x, y in zip(a[2:], b[2:]):
+                    np.testing.assert_allclose(x, y, rtol=0, atol=1e-13)
