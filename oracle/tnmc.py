@@ -627,3 +627,79 @@ def frozen_line_step(Jh, Jv, h, beta, chi, chains, kr, kc, px, py, seed, step, T
         for k, i in enumerate(idx):
             sp[i][np.ix_(rows, cols)] = cur[k]
     return sp, acc
+
+
+# ---- the bond-basis gauge of App. A (a builder variant that changes q) ----
+
+def vertical_split(J, beta):
+    """W = B T for the vertical bond weight W[s, s'] = exp(beta J s s') (App. A: each W is
+    split by its SVD into a factor for each end).  W is symmetric with eigenvectors
+    u_0 = (1, 1)/sqrt 2 and u_1 = (1, -1)/sqrt 2 (index 0 <-> s = -1) and eigenvalues
+    2 cosh(beta J), 2 sinh(beta J); B[s, rho] = u_rho(s) sqrt|lambda_rho| and
+    T[rho, s'] = sign(lambda_rho) sqrt|lambda_rho| u_rho(s').  Returns (B, T)."""
+    lam = np.array([2.0 * math.cosh(beta * J), 2.0 * math.sinh(beta * J)])
+    U = np.array([[1.0, 1.0], [1.0, -1.0]]) / math.sqrt(2.0)       # U[s, rho]
+    root = np.sqrt(np.abs(lam))
+    B = U * root[None, :]
+    T = (np.sign(lam) * root)[:, None] * U.T
+    return B, T
+
+
+def row_tensors_bond(envb_next, Jh, Jv, h, beta, r):
+    """D_r H_r V'_r env'_{r+1}: row r's site tensors (physical index: row r's spins) with the
+    lower factor B of each vertical bond (r, r+1) applied to the bond-basis boundary MPS
+    env'_{r+1} (physical index: the vertical bond).  Same index layout as apply_row_mpo."""
+    Ly, Lx = h.shape
+    P = []
+    for c in range(Lx):
+        if envb_next is None:
+            t = np.ones((1, 2, 1))
+        else:
+            Bv, _ = vertical_split(Jv[r, c], beta)
+            t = np.einsum("sp,apb->asb", Bv, envb_next[c])
+        t = t * np.exp(beta * h[r, c] * SPIN)[None, :, None]
+        Dl, _, Dr = t.shape
+        if c > 0:
+            G = np.exp(beta * Jh[r, c - 1] * np.outer(SPIN, SPIN))
+            t = np.einsum("asb,ks->aksb", t, G).reshape(Dl * 2, 2, Dr)
+            Dl *= 2
+        if c < Lx - 1:
+            t2 = np.zeros((Dl, 2, Dr, 2))
+            for s in range(2):
+                t2[:, s, :, s] = t[:, s, :]
+            t = t2.reshape(Dl, 2, Dr * 2)
+        P.append(t)
+    return P
+
+
+def build_env_bond(Jh, Jv, h, beta, chi):
+    """Environments in the bond-basis gauge (App. A, eqs. pf_bond_description to
+    pf_vertex_description): the boundary MPS carries the vertical bond indices, is built
+    bottom-up as env'_r = T_chi[ T_{r-1} D_r H_r V'_r env'_{r+1} ] (T_{r-1}: the upper factor
+    of the bonds between rows r-1 and r, applied on the physical leg before truncating),
+    and row r is sampled from the untruncated M'_r = D_r H_r V'_r env'_{r+1} (bond up to 2 chi;
+    the rows above enter through W(s_up, s) = sum_rho B(s_up, rho) T(rho, s) = f(s), as in the
+    spin basis).  env.M holds the M'_r; log Z~ = sum_{r >= 1} log_scale[r] + log of the
+    contraction of M'_0 over row 0's spins."""
+    Jh, Jv, h, Lx, Ly = _check_lattice(Jh, Jv, h)
+    env = Env(Lx, Ly, float(beta), int(chi), Jh, Jv, h)
+    nxt = None
+    for r in range(Ly - 1, -1, -1):
+        P = row_tensors_bond(nxt, Jh, Jv, h, beta, r)
+        env.M[r] = P
+        if r > 0:
+            X = []
+            for c in range(Lx):
+                _, Tv = vertical_split(Jv[r - 1, c], beta)
+                X.append(np.einsum("ps,asb->apb", Tv, P[c]))
+            nxt, env.log_scale[r] = truncate_row(X, chi, Lx, Ly, r, env)
+    v = np.ones(1)
+    logv = 0.0
+    for c in range(Lx):
+        v = v @ (env.M[0][c][:, 0, :] + env.M[0][c][:, 1, :])
+        m = np.abs(v).max()
+        if m > 0:
+            v = v / m
+            logv += math.log(m)
+    env.logZ = float(np.sum(env.log_scale[1:])) + logv + math.log(v[0]) if v[0] > 0 else float("nan")
+    return env
