@@ -49,16 +49,24 @@ TABLE_HB = {"thresholds": [0.25, 0.15, 0.05, 0.025], "tnmh_plus_metropolis": [3,
 TABLE_HBPBC = {"thresholds": [0.25, 0.15, 0.05, 0.025], "tnmh": [14, 21, 40, 56]}
 
 
-def algorithmic_flops(inst):
+def algorithmic_flops(inst, gauge="spin"):
     """8 chi_c chi_{c+1} FLOP per site per sample for rows r >= 1, 4 chi chi' for row 0
-    (its right sweep does not depend on the sample): the left and right sweeps."""
-    from paper_2104_13264_gb300.instances import Instance  # noqa: F401
+    (its right sweep does not depend on the sample): the left and right sweeps.  In the
+    bond gauge row r is sampled from bonds 2 chi'_c of the truncated env'_{r+1} (2 on the
+    last row)."""
     Lx, Ly, chi = inst.Lx, inst.Ly, inst.chi
 
-    def bd(r, c):
+    def bd_env(r, c):
         if c <= 0 or c >= Lx:
             return 1
         return min(chi, 1 << min(c, Lx - c, Ly - r, 30))
+
+    def bd(r, c):
+        if gauge == "spin":
+            return bd_env(r, c)
+        if c <= 0 or c >= Lx:
+            return 1
+        return 2 * (bd_env(r + 1, c) if r + 1 < Ly else 1)
 
     tot = 0
     for r in range(Ly):
@@ -157,7 +165,8 @@ def run_tnmc(args):
     dev = torch.device("cuda", local)
 
     t0 = time.time()
-    env = Bd.Env.from_instance(inst, precisions=tuple(sorted({"f64", prec} | ({"f32"} if args.tune_steps else set()))))
+    env = Bd.Env.from_instance(inst, precisions=tuple(sorted({"f64", prec} | ({"f32"} if args.tune_steps else set()))),
+                               gauge=args.gauge)
     info = env.info()
     env_build_s = time.time() - t0
     tuning = None
@@ -297,7 +306,7 @@ def run_tnmc(args):
             pg.destroy_process_group()
         return
     peaks, peak_src = load_peaks()
-    flops = algorithmic_flops(inst)
+    flops = algorithmic_flops(inst, args.gauge)
     kern_s = statistics.mean(sample_ms) / 1e3
     achieved_tf = flops * B / kern_s / 1e12
     smmax = float(peaks.get("sm_max_mhz", 2070.0))
@@ -349,6 +358,7 @@ def run_tnmc(args):
         "data": "synthetic (seeded instance generator)",
         "config": {"workload": args.config, "description": desc, "Lx": inst.Lx, "Ly": inst.Ly, "chi": inst.chi,
                    "beta": inst.beta, "B": B, "chains": C, "proposals_per_chain": T, "precision": prec,
+                   "gauge": args.gauge,
                    "parallelism": "replicas%d" % world,
                    "l2": "flushed (256 MiB write between steps)" if flush is not None else "outputs > L2"},
         "proposals_per_s": round(props_s, 3), "acceptance": round(acc_rate, 5),
@@ -943,6 +953,8 @@ def main():
     ap.add_argument("--plain-batch", type=int, default=2 * 152 * 64)   # one full wave of the FP64 kernel
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--iters", type=int, default=30, help="iterations of the Delta trajectory (c3d)")
+    ap.add_argument("--gauge", default="spin", choices=["spin", "bond"],
+                    help="environment gauge: spin basis, or the bond basis of App. A (chi <= 32)")
     ap.add_argument("--tune-steps", type=int, default=0,
                     help="tuning steps of the FP32 tensors before the timed sampling (the 64x64 Villain case uses 50)")
     args = ap.parse_args()

@@ -20,7 +20,9 @@
  *     ordered on one stream (calls that overlap on the GPU race).
  *   - Numerical trouble found on the device (a non-positive or non-finite
  *     conditional normaliser, a zero environment) is reported per sample in
- *     `flags` and in the env's status word, read with tnmc_env_status.
+ *     `flags` and in the env's status word, read with tnmc_env_status.  A flagged
+ *     sample keeps a finite log q (the probability it was drawn with) and takes part
+ *     in MH like any other; it contributes nothing to tnmc_logq_backward.
  *   - Random numbers come from Philox4x32-10 (Salmon et al., SC'11) keyed by
  *     the 64-bit seed; counters:
  *       draw of (site, sample) (site/2, sample_lo, sample_hi, 0), words
@@ -137,6 +139,25 @@ const char* tnmc_last_error(void);
 tnmc_status tnmc_build_env(const tnmc_lattice* lat, double beta, int chi, int precision_mask,
                            void* stream, tnmc_env** out);
 
+/*
+ * The same environments in the paper's bond-basis gauge (App. A, eqs. pf_bond_description
+ * to pf_vertex_description), a builder variant that defines another q.  Each vertical bond
+ * weight is split as W = B T by its SVD (W = sum_rho lambda_rho u_rho u_rho^T with
+ * u_0 = (1,1)/sqrt 2, u_1 = (1,-1)/sqrt 2, index 0 <-> s = -1, lambda = 2 cosh, 2 sinh of
+ * beta J; B[s][rho] = u_rho(s) sqrt|lambda_rho|, T[rho][s] = sign(lambda_rho) sqrt|lambda_rho|
+ * u_rho(s)), and the boundary MPS carries the vertical bond index rho:
+ *   env'_r = T_chi[ T_{r-1} D_r H_r V'_r env'_{r+1} ]   (V' applies B; T_{r-1} the upper factor
+ *   of the bonds above row r, on the physical leg, before truncating),
+ * while row r is sampled from the untruncated M'_r = D_r H_r V'_r env'_{r+1}, an MPS of the
+ * row's spins with bonds up to 2 chi (the rows above enter through the same field factors
+ * f(s) = W(s_up, s)).  The samplers, MH and backward run on it unchanged.  log Z~ (env_info)
+ * is this gauge's; log_scale, sv and discarded (env_export) describe the truncations of
+ * env'_r for r >= 1 (row 0's entries are not used).  chi <= 32 (bonds up to 64); always the
+ * dense (non-parity) builder.  Arguments as tnmc_build_env.
+ */
+tnmc_status tnmc_build_env_bond(const tnmc_lattice* lat, double beta, int chi, int precision_mask, void* stream,
+                                tnmc_env** out);
+
 tnmc_status tnmc_env_free(tnmc_env* env);
 
 /* Synchronises the env's build stream and fills `info`. */
@@ -167,7 +188,10 @@ tnmc_status tnmc_env_status(const tnmc_env* env, int32_t* status);
  * precision   which sampler copy to use (must be present in the env)
  * B           number of proposals, >= 0; sample index of row b is sample_offset + b
  * spins       device int8 [B][Ly][Lx] (output)
- * logq        device double [B] (output; -inf for flagged samples)
+ * logq        device double [B] (output).  A site whose normaliser w_+ + w_- is not
+ *             positive or not finite is drawn with p_+ = 1/2 and contributes log 1/2;
+ *             the sample is flagged, and its log q is still the log of the probability
+ *             it was drawn with, so q is the exact law of the sampler.
  * energy      device double [B] (output)
  * flags       device int32 [B] or NULL (output; TNMC_FLAG_NUMERIC)
  * The first call on an env may allocate device scratch for the per-sample

@@ -228,7 +228,10 @@ def run(env, B, seed=0, sample_offset=0, forced=None, keep=False, samples=None):
     Sample b uses Philox sample index sample_offset + b, or samples[b] when an
     explicit index array is given.  Returns (spins int8 [B, Ly, Lx], logq [B],
     energy [B], flags [B]) and, with keep=True, the per-row forward record
-    used by the gradient.
+    used by the gradient.  A site whose normaliser w_+ + w_- is not positive or not
+    finite is drawn with p = 1/2, adds log 1/2 to log q and sets the sample's flag:
+    log q stays the log of the probability the sample was drawn with, so q is the
+    exact law of the procedure and MH stays exact.
     """
     Lx, Ly = env.Lx, env.Ly
     spins = np.zeros((B, Ly, Lx), dtype=np.int8) if forced is None else np.asarray(forced, dtype=np.int8)
@@ -278,7 +281,6 @@ def run(env, B, seed=0, sample_offset=0, forced=None, keep=False, samples=None):
                 Lam[c + 1] = _pow2_normalize(U[np.arange(B), idx, :] * f[np.arange(B), c, idx][:, None])
             if keep:
                 record.append((f, R, Lam, wraw))
-    logq = np.where(flags != 0, -np.inf, logq)
     E = energy(env.Jh, env.Jv, env.h, spins)
     if keep:
         return spins, logq, E, flags, record

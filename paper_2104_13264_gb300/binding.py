@@ -50,6 +50,7 @@ _INT = ctypes.c_int
 SIGNATURES = {
     "tnmc_last_error": ([], ctypes.c_char_p),
     "tnmc_build_env": ([ctypes.POINTER(_Lattice), ctypes.c_double, _INT, _INT, _P, ctypes.POINTER(_P)], _INT),
+    "tnmc_build_env_bond": ([ctypes.POINTER(_Lattice), ctypes.c_double, _INT, _INT, _P, ctypes.POINTER(_P)], _INT),
     "tnmc_env_free": ([_P], _INT),
     "tnmc_env_info": ([_P, ctypes.POINTER(_Info)], _INT),
     "tnmc_env_export": ([_P, _P, _P, _P, _P, _P], _INT),
@@ -146,7 +147,7 @@ def _ptr(t):
 class Env:
     """FP64-built row environments of one instance (owned by the library)."""
 
-    def __init__(self, Jh, Jv, h, beta, chi, precisions=("f64",), stream=None):
+    def __init__(self, Jh, Jv, h, beta, chi, precisions=("f64",), stream=None, gauge="spin"):
         h = np.ascontiguousarray(h, dtype=np.float64)
         Ly, Lx = h.shape
         Jh = np.ascontiguousarray(np.asarray(Jh, dtype=np.float64).reshape(Ly, max(Lx - 1, 0)))
@@ -159,7 +160,8 @@ class Env:
                        h.ctypes.data)
         out = ctypes.c_void_p()
         self._h = None
-        _check(lib().tnmc_build_env(ctypes.byref(lat), self.beta, self.chi, mask, _stream(stream), ctypes.byref(out)))
+        build = {"spin": lib().tnmc_build_env, "bond": lib().tnmc_build_env_bond}[gauge]
+        _check(build(ctypes.byref(lat), self.beta, self.chi, mask, _stream(stream), ctypes.byref(out)))
         self._h = out
 
     @classmethod
@@ -170,8 +172,8 @@ class Env:
         return self
 
     @classmethod
-    def from_instance(cls, inst, precisions=("f64",), chi=None, stream=None):
-        return cls(inst.Jh, inst.Jv, inst.h, inst.beta, inst.chi if chi is None else chi, precisions, stream)
+    def from_instance(cls, inst, precisions=("f64",), chi=None, stream=None, gauge="spin"):
+        return cls(inst.Jh, inst.Jv, inst.h, inst.beta, inst.chi if chi is None else chi, precisions, stream, gauge)
 
     @property
     def handle(self):

@@ -87,7 +87,7 @@ namespace {
 
 // Checks the arguments, allocates the environment's arena and uploads the
 // couplings; the tensors are written by a later builder launch.
-tnmc_status env_create(const tnmc_lattice* lat, double beta, int chi, int precision_mask, cudaStream_t s,
+tnmc_status env_create(const tnmc_lattice* lat, double beta, int chi, int precision_mask, int gauge, cudaStream_t s,
                        tnmc_env** out) {
   using namespace tnmc;
   *out = nullptr;
@@ -95,6 +95,8 @@ tnmc_status env_create(const tnmc_lattice* lat, double beta, int chi, int precis
   const int Lx = lat->Lx, Ly = lat->Ly;
   CHECK_ARG(Lx >= 1 && Ly >= 1 && Lx <= 4096 && Ly <= 4096, "lattice %d x %d out of range", Ly, Lx);
   CHECK_ARG(chi >= 1 && chi <= kMaxChi, "chi = %d must be in [1, %d]", chi, kMaxChi);
+  CHECK_ARG(gauge == 0 || chi <= kMaxChi / 2, "the bond basis samples from 2 chi bonds: chi = %d must be <= %d", chi,
+            kMaxChi / 2);
   CHECK_ARG(isfinite(beta) && beta >= 0.0, "beta must be finite and >= 0");
   CHECK_ARG(lat->h, "h must be non-null");
   CHECK_ARG(Lx == 1 || lat->Jh, "Jh must be non-null when Lx > 1");
@@ -112,7 +114,8 @@ tnmc_status env_create(const tnmc_lattice* lat, double beta, int chi, int precis
       const int b = bond_dim_host(chi, Lx, Ly, r, c);
       if (b > maxb) maxb = b;
     }
-  const int P = pad4(maxb);
+  // the bond basis samples each row from its untruncated MPS: bonds up to 2 chi
+  const int P = pad4(gauge ? 2 * maxb : maxb);
   const size_t ntens = (size_t)Lx * Ly;
   const size_t tens = ntens * P * 2 * P;
   // arena layout
@@ -163,8 +166,9 @@ tnmc_status env_create(const tnmc_lattice* lat, double beta, int chi, int precis
     bool zero_field = true;
     for (size_t i = 0; i < nh; ++i) zero_field = zero_field && (lat->h[i] == 0.0);
     const char* force = getenv("TNMC_DENSE_BUILDER");   // testing knob: the dense path on h = 0 lattices
-    d.z2 = zero_field && !(force && force[0] == '1');
+    d.z2 = zero_field && !(force && force[0] == '1') && gauge == 0;
   }
+  d.gauge = gauge;
   d.Jh = reinterpret_cast<const double*>(base + oJh);
   d.Jv = reinterpret_cast<const double*>(base + oJv);
   d.h = reinterpret_cast<const double*>(base + oh);
@@ -229,15 +233,15 @@ extern "C" {
 
 const char* tnmc_last_error(void) { return g_err; }
 
-tnmc_status tnmc_build_env(const tnmc_lattice* lat, double beta, int chi, int precision_mask, void* stream,
-                           tnmc_env** out) {
+static tnmc_status build_env_gauge(const tnmc_lattice* lat, double beta, int chi, int precision_mask, int gauge,
+                                   void* stream, tnmc_env** out) {
   using namespace tnmc;
   g_err[0] = 0;
   CHECK_ARG(lat && out, "lat and out must be non-null");
   *out = nullptr;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   tnmc_env* env = nullptr;
-  tnmc_status st = env_create(lat, beta, chi, precision_mask, s, &env);
+  tnmc_status st = env_create(lat, beta, chi, precision_mask, gauge, s, &env);
   if (st != TNMC_OK) return st;
   const DeviceEnv& d = env->d;
   void* work = nullptr;
@@ -251,6 +255,8 @@ tnmc_status tnmc_build_env(const tnmc_lattice* lat, double beta, int chi, int pr
     }
     st = tnmc_launch_build(env, s, work, wbytes);
     if (st != TNMC_OK) break;
+    if (gauge == 1) st = tnmc_launch_bond_sampling(env, s);
+    if (st != TNMC_OK) break;
     st = env_derive(env, s);
   } while (0);
   dev_free(env->alloc, work, wbytes, s);
@@ -261,6 +267,16 @@ tnmc_status tnmc_build_env(const tnmc_lattice* lat, double beta, int chi, int pr
   }
   *out = env;
   return TNMC_OK;
+}
+
+tnmc_status tnmc_build_env(const tnmc_lattice* lat, double beta, int chi, int precision_mask, void* stream,
+                           tnmc_env** out) {
+  return build_env_gauge(lat, beta, chi, precision_mask, 0, stream, out);
+}
+
+tnmc_status tnmc_build_env_bond(const tnmc_lattice* lat, double beta, int chi, int precision_mask, void* stream,
+                                tnmc_env** out) {
+  return build_env_gauge(lat, beta, chi, precision_mask, 1, stream, out);
 }
 
 tnmc_status tnmc_build_env_batched(int n, const tnmc_lattice* lats, const double* beta, const int* chi,
@@ -277,7 +293,7 @@ tnmc_status tnmc_build_env_batched(int n, const tnmc_lattice* lats, const double
   tnmc_status st = TNMC_OK;
   size_t wtotal = 0;
   for (int i = 0; i < n && st == TNMC_OK; ++i) {
-    st = env_create(&lats[i], beta[i], chi[i], precision_mask, s, &envs[i]);
+    st = env_create(&lats[i], beta[i], chi[i], precision_mask, 0, s, &envs[i]);
     if (st != TNMC_OK) {
       char msg[512];
       snprintf(msg, sizeof msg, "instance %d: %s", i, g_err);

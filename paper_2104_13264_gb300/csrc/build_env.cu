@@ -45,7 +45,23 @@ struct BuildArgs {
   int32_t* status;
   int32_t* esz;   // [Ly][Lx+1] even-sector size of every bond (Z2 builder)
   int z2;         // parity-sector builder (all fields zero)
+  int gauge;      // 1: bond basis (vertical bonds split as W = B T)
 };
+
+// The split W = B T of a vertical bond weight W[s][s'] = exp(beta J s s') (App. A): W has
+// eigenvectors u_0 = (1, 1)/sqrt 2, u_1 = (1, -1)/sqrt 2 (index 0 <-> s = -1) with
+// eigenvalues 2 cosh(beta J), 2 sinh(beta J); B[s][rho] = u_rho(s) sqrt|lambda_rho|,
+// T[rho][s] = sign(lambda_rho) sqrt|lambda_rho| u_rho(s).
+__host__ __device__ inline double split_B(double bj, int s, int rho) {
+  const double lam = rho ? 2.0 * sinh(bj) : 2.0 * cosh(bj);
+  const double u = (rho && s) ? -0.70710678118654752440 : 0.70710678118654752440;
+  return u * sqrt(fabs(lam));
+}
+__host__ __device__ inline double split_T(double bj, int rho, int s) {
+  const double lam = rho ? 2.0 * sinh(bj) : 2.0 * cosh(bj);
+  const double u = (rho && s) ? -0.70710678118654752440 : 0.70710678118654752440;
+  return (lam < 0.0 ? -1.0 : 1.0) * sqrt(fabs(lam)) * u;
+}
 
 
 __device__ inline double warp_sum(double v) {
@@ -128,6 +144,27 @@ __device__ void apply_row_mpo(const BuildArgs& a, Shared& sh, int r) {
     const double* Mn = last_row ? nullptr : a.M64 + ((size_t)(r + 1) * Lx + c) * P * 2 * P;
     double* out = a.work + (size_t)c * slot_sz;
     const int total = Dl * 2 * Dr;
+    const double bjd = last_row ? 0.0 : a.beta * a.Jv[r * Lx + c];              // bond (r, r+1)
+    const double bju = (r > 0) ? a.beta * a.Jv[(r - 1) * Lx + c] : 0.0;         // bond (r-1, r)
+    // site value for row-r spin s (before any upper factor)
+    auto site = [&](int s, int aa, int k, int b, int kp) -> double {
+      if (!(kr == 1 || kp == s)) return 0.0;
+      double n;
+      if (last_row) {
+        n = 1.0;
+      } else if (a.gauge == 1) {
+        // the lower factor of bond (r, r+1) on the boundary MPS's bond index rho
+        n = split_B(bjd, s, 0) * Mn[((size_t)aa * 2 + 0) * P + b] + split_B(bjd, s, 1) * Mn[((size_t)aa * 2 + 1) * P + b];
+      } else {
+        // sum over the spin s' of row r+1: W[s][s'] = exp(beta Jv s s')
+        const double m0 = Mn[((size_t)aa * 2 + 0) * P + b];
+        const double m1 = Mn[((size_t)aa * 2 + 1) * P + b];
+        n = s ? (vd * m0 + vs * m1) : (vs * m0 + vd * m1);
+      }
+      double val = n * (s ? hp : hm);
+      if (kl == 2) val *= (k == s) ? gs : gd;
+      return val;
+    };
     for (int idx = lane; idx < total; idx += 32) {
       const int rr = idx % Dr;
       const int s = (idx / Dr) & 1;
@@ -135,19 +172,12 @@ __device__ void apply_row_mpo(const BuildArgs& a, Shared& sh, int r) {
       int aa = l, k = 0, b = rr, kp = 0;
       if (kl == 2) { aa = l >> 1; k = l & 1; }
       if (kr == 2) { b = rr >> 1; kp = rr & 1; }
-      double val = 0.0;
-      if (kr == 1 || kp == s) {
-        double n;
-        if (last_row) {
-          n = 1.0;
-        } else {
-          // sum over the spin s' of row r+1: W[s][s'] = exp(beta Jv s s')
-          const double m0 = Mn[((size_t)aa * 2 + 0) * P + b];
-          const double m1 = Mn[((size_t)aa * 2 + 1) * P + b];
-          n = s ? (vd * m0 + vs * m1) : (vs * m0 + vd * m1);
-        }
-        val = n * (s ? hp : hm);
-        if (kl == 2) val *= (k == s) ? gs : gd;
+      double val;
+      if (a.gauge == 1 && r > 0) {
+        // bond basis: the physical index becomes rho of bond (r-1, r), through its upper factor
+        val = split_T(bju, s, 0) * site(0, aa, k, b, kp) + split_T(bju, s, 1) * site(1, aa, k, b, kp);
+      } else {
+        val = site(s, aa, k, b, kp);
       }
       out[idx] = val;
     }
@@ -1103,8 +1133,97 @@ __global__ void __launch_bounds__(kBuildThreads) build_env_batched_kernel(const 
   else build_env_body(a, smem);
 }
 
+// Bond basis: the sampling tensors M'_r = D_r H_r V'_r env'_{r+1} of every row (the
+// untruncated MPS of the row's spins, bond up to 2 chi), from the bond-basis boundary MPS
+// env' the builder left in M64 (bond dims in `bond`), into `out` ([Ly][Lx][P][2][P], zero
+// padded), and their bond dims into `nb`.  Same index layout as the builder's row MPO.
+__global__ void bond_sampling_kernel(DeviceEnv d, const int32_t* bond, double* out, int32_t* nb) {
+  const int Lx = d.Lx, Ly = d.Ly, P = d.P;
+  const size_t per = (size_t)P * 2 * P;
+  const size_t total = (size_t)Lx * Ly * per;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t t = i / per;
+    const int rem = (int)(i % per);
+    const int rr = rem % P, s = (rem / P) & 1, l = rem / (2 * P);
+    const int r = (int)(t / Lx), c = (int)(t % Lx);
+    const bool last_row = (r == Ly - 1);
+    const int Dl0 = last_row ? 1 : bond[(r + 1) * (Lx + 1) + c];
+    const int Dr0 = last_row ? 1 : bond[(r + 1) * (Lx + 1) + c + 1];
+    const int kl = (c > 0) ? 2 : 1, kr = (c < Lx - 1) ? 2 : 1;
+    const int Dl = Dl0 * kl, Dr = Dr0 * kr;
+    if (rem == 0) {
+      nb[r * (Lx + 1) + c] = Dl;
+      if (c == Lx - 1) nb[r * (Lx + 1) + Lx] = 1;
+    }
+    double val = 0.0;
+    if (l < Dl && rr < Dr) {
+      int aa = l, k = 0, b = rr, kp = 0;
+      if (kl == 2) { aa = l >> 1; k = l & 1; }
+      if (kr == 2) { b = rr >> 1; kp = rr & 1; }
+      if (kr == 1 || kp == s) {
+        double n = 1.0;
+        if (!last_row) {
+          const double bj = d.beta * d.Jv[r * Lx + c];
+          const double* Mn = d.M64 + ((size_t)(r + 1) * Lx + c) * per;
+          n = split_B(bj, s, 0) * Mn[((size_t)aa * 2 + 0) * P + b] + split_B(bj, s, 1) * Mn[((size_t)aa * 2 + 1) * P + b];
+        }
+        const double hv = d.beta * d.h[r * Lx + c];
+        val = n * exp(s ? hv : -hv);
+        if (kl == 2) val *= exp(d.beta * d.Jh[r * (Lx - 1) + c - 1] * ((k == s) ? 1.0 : -1.0));
+      }
+    }
+    out[i] = val;
+  }
+}
+
+// log Z~ of the bond basis: sum_{r >= 1} log_scale[r] + log of the contraction of M'_0 over
+// row 0's spins (one warp).
+__global__ void bond_logz_kernel(DeviceEnv d, const double* log_scale, double* logZ) {
+  const int lane = threadIdx.x, Lx = d.Lx, P = d.P;
+  __shared__ double v[kMaxPad], v2[kMaxPad];
+  for (int i = lane; i < P; i += 32) v[i] = (i == 0) ? 1.0 : 0.0;
+  __syncwarp();
+  double logv = 0.0;
+  for (int c = 0; c < Lx; ++c) {
+    const double* M = d.M64 + (size_t)c * P * 2 * P;
+    const int Dl = d.bond[c], Dr = d.bond[c + 1];
+    double mx = 0.0;
+    for (int b = lane; b < Dr; b += 32) {
+      double acc = 0.0;
+      for (int aa = 0; aa < Dl; ++aa) acc += v[aa] * (M[((size_t)aa * 2) * P + b] + M[((size_t)aa * 2 + 1) * P + b]);
+      v2[b] = acc;
+      mx = fmax(mx, fabs(acc));
+    }
+    mx = warp_max(mx);
+    __syncwarp();
+    for (int b = lane; b < P; b += 32) v[b] = (b < Dr && mx > 0.0) ? v2[b] / mx : 0.0;
+    if (mx > 0.0) logv += log(mx);
+    __syncwarp();
+  }
+  if (lane == 0) {
+    double tot = 0.0;
+    for (int r = 1; r < d.Ly; ++r) tot += log_scale[r];
+    *logZ = (v[0] > 0.0) ? tot + logv + log(v[0]) : NAN;
+  }
+}
+
 }  // namespace
 }  // namespace tnmc
+
+tnmc_status tnmc_launch_bond_sampling(tnmc_env* env, cudaStream_t stream) {
+  using namespace tnmc;
+  DeviceEnv& d = env->d;
+  const size_t bytes = (size_t)d.Lx * d.Ly * d.P * 2 * d.P * sizeof(double);
+  const size_t bb = (size_t)d.Ly * (d.Lx + 1) * sizeof(int32_t);
+  // R64 (derived later) is free scratch now; esz is unused by the dense builder
+  bond_sampling_kernel<<<1024, 256, 0, stream>>>(d, d.bond, const_cast<double*>(d.R64), env->esz);
+  TNMC_CUDA_TRY(cudaGetLastError());
+  TNMC_CUDA_TRY(cudaMemcpyAsync(const_cast<double*>(d.M64), d.R64, bytes, cudaMemcpyDeviceToDevice, stream));
+  TNMC_CUDA_TRY(cudaMemcpyAsync(const_cast<int32_t*>(d.bond), env->esz, bb, cudaMemcpyDeviceToDevice, stream));
+  bond_logz_kernel<<<1, 32, 0, stream>>>(d, env->log_scale, env->logZ);
+  TNMC_CUDA_TRY(cudaGetLastError());
+  return TNMC_OK;
+}
 
 size_t tnmc_build_work_bytes(int Lx, int Ly, int P) {
   (void)Ly;
@@ -1137,6 +1256,7 @@ static tnmc::BuildArgs make_build_args(tnmc_env* env, void* work) {
   a.status = d.status;
   a.esz = env->esz;
   a.z2 = d.z2;
+  a.gauge = d.gauge;
   return a;
 }
 

@@ -29,6 +29,7 @@ struct DeviceEnv {
   double beta;
   int integer_couplings;
   int z2;             // 1 when every field is zero: the builder uses parity sectors
+  int gauge;          // 0: spin basis; 1: bond basis (rows sampled from the untruncated 2 chi MPS)
   const double* Jh;   // device copies of the couplings
   const double* Jv;
   const double* h;
@@ -178,6 +179,7 @@ tnmc_status tnmc_launch_build_batched(tnmc_env* const* envs, int n, void* work, 
 size_t tnmc_build_args_bytes();
 size_t tnmc_build_work_bytes(int Lx, int Ly, int P);
 tnmc_status tnmc_launch_derive(tnmc_env* env, int precision_mask, cudaStream_t stream);
+tnmc_status tnmc_launch_bond_sampling(tnmc_env* env, cudaStream_t stream);
 tnmc_status tnmc_launch_sample(const tnmc_env* env, int precision, int64_t B, uint64_t seed,
                                uint64_t sample_offset, const int8_t* spins_in, int8_t* spins_out,
                                double* logq, double* energy, int32_t* flags, cudaStream_t stream);

@@ -254,7 +254,9 @@ __device__ void sample_simt_tile(const SampleArgs<T>& a, int64_t tile, unsigned 
       for (int wd = 0; wd < W; ++wd) bits_prev[wd * NT + tid] = bits_cur[wd * NT + tid];
     }
     if (active) {
-      a.logq[b] = flag ? -INFINITY : acc.value();
+      // a flagged sample keeps the log of the probability it was drawn with (log 1/2 at a
+      // site whose normaliser failed): q stays the exact law of the sampler
+      a.logq[b] = acc.value();
       a.energy[b] = E;
       if (a.flags) a.flags[b] = flag;
       if (flag) set_status(a.e.status, TNMC_E_NUMERIC);

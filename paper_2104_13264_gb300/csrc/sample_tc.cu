@@ -500,7 +500,7 @@ __global__ void __launch_bounds__(kThreads, 2) sample_tc_kernel(TcArgs a) {
       __syncthreads();   // bits_prev is read by both halves in the next row
     }
     if (h == 0 && active && !abort) {
-      a.logq[b] = flag ? -INFINITY : lq;
+      a.logq[b] = lq;   // flagged samples too: the log of the probability they were drawn with
       a.energy[b] = E;
       if (a.flags) a.flags[b] = flag;
       if (flag) set_status(a.e.status, TNMC_E_NUMERIC);

@@ -198,9 +198,10 @@ def test_config3_full_size_sampled(B):
         assert torch.equal(plan.view(run.prop[0], i), ref[0])
         assert torch.equal(plan.rows(run.prop[1], i), ref[1])
     # FP32 at beta = 2 may lose a conditional to rounding (both weights clamp to 0): such
-    # proposals are flagged, carry log q = -inf and are always rejected
+    # proposals are flagged and drawn with p = 1/2 at that site, which their finite log q
+    # records, so they stay in the chain's exact proposal law
     lq, fl = run.prop[1], run.prop[3]
-    assert torch.equal(~torch.isfinite(lq), fl != 0)
+    assert bool(torch.isfinite(lq).all())
     frac = float((fl != 0).double().mean())
     bad = sorted({i for i in range(plan.n) if bool((plan.rows(fl, i) != 0).any())})
     print("flagged fraction %.3g in %d instances %s" % (frac, len(bad), bad[:20]))

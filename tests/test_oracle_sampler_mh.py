@@ -213,3 +213,27 @@ def test_init_chain_bits():
     sp = philox.init_bits(5, 300, np.arange(4))
     assert set(np.unique(sp)) <= {-1, 1}
     assert 0.4 < (sp > 0).mean() < 0.6
+
+
+def test_flagged_samples_keep_their_draw_probability():
+    """Signed tensors make both weights of some conditionals clamp to zero; such a site is
+    drawn with p = 1/2.  q must remain the exact law of the procedure: summed over every
+    configuration it is 1 including the flagged ones, and the sampler's draws follow it."""
+    Ly, Lx = 2, 3
+    shapes = [(tnmc.bond_dim(2, Lx, Ly, r, c), 2, tnmc.bond_dim(2, Lx, Ly, r, c + 1))
+              for r in range(Ly) for c in range(Lx)]
+    ts = instances.random_tensors(shapes, seed=3, positive=False)
+    inst = instances.random_small(Ly, Lx, 0.7, 2, seed=4)
+    env = tnmc.Env(Lx, Ly, inst.beta, 2, inst.Jh, inst.Jv, inst.h)
+    env.M = [[ts[r * Lx + c] for c in range(Lx)] for r in range(Ly)]
+    S = exact.all_states(Ly, Lx)
+    _, lq, _, fl = tnmc.logq(env, S)
+    assert fl.any() and (fl == 0).any()
+    assert np.exp(lq).sum() == pytest.approx(1.0, abs=1e-12)
+    sp, lq2, _, fl2 = tnmc.sample(env, 200_000, seed=5)
+    idx = ((sp.reshape(len(sp), -1) > 0).astype(np.int64) << np.arange(Ly * Lx)).sum(axis=1)
+    counts = np.bincount(idx, minlength=len(S))
+    np.testing.assert_allclose(lq2, lq[idx], rtol=0, atol=1e-12)
+    e = len(sp) * np.exp(lq)
+    keep = e > 5
+    assert stats.chi2.sf(((counts[keep] - e[keep]) ** 2 / e[keep]).sum(), keep.sum() - 1) > 1e-3
