@@ -333,9 +333,9 @@ def run_tnmc(args):
     traffic = None
     if prec == "bf16":
         # DRAM bytes (read + write) per proposal and row of the tensor-core kernel, from ncu on
-        # the 16x256 chi = 64 strip (74.20 + 68.46 GB for 65536 proposals x 16 rows); the
+        # the 16x256 chi = 64 strip (69.91 + 68.46 GB for 65536 proposals x 16 rows); the
         # right stack dominates it and grows in proportion to proposals x rows
-        traffic = round(136_000.0 * B * inst.Ly)
+        traffic = round(131_960.0 * B * inst.Ly)
     roof.update({"traffic": traffic, "kernel": "sample_%s" % prec, "kernel_ms": round(kern_s * 1e3, 3)})
     step_ms = total_ms / args.steps
     props_s = B * world / (step_ms / 1e3)
