@@ -705,3 +705,117 @@ def build_env_bond(Jh, Jv, h, beta, chi):
             logv += math.log(m)
     env.logZ = float(np.sum(env.log_scale[1:])) + logv + math.log(v[0]) if v[0] > 0 else float("nan")
     return env
+
+
+# ---- two-site variational compression (App. A: the alternative to successive SVD) ----
+
+def _left_overlap(Lenv, Y, X):
+    """<Y_0..Y_c | X_0..X_c> from <Y_0..Y_{c-1} | X_0..X_{c-1}>: [ay, ax] -> [by, bx]."""
+    return np.einsum("ab,asc,bsd->cd", Lenv, Y, X)
+
+
+def _right_overlap(Renv, Y, X):
+    """<Y_c.. | X_c..> from <Y_{c+1}.. | X_{c+1}..>: [by, bx] -> [ay, ax]."""
+    return np.einsum("asc,bsd,cd->ab", Y, X, Renv)
+
+
+def _rescaled(T):
+    m = float(np.abs(T).max())
+    if not m > 0:
+        raise FloatingPointError("zero overlap environment")
+    return T / m, math.log(m)
+
+
+def truncate_row_variational(P, chi, Lx, Ly, r, sweeps, env=None):
+    """T_chi by two-site variational compression (App. A names it beside successive SVD).
+
+    The row X = P (the exact MPO-MPS product) is approximated by an MPS Y with the
+    static bond dims of bond_dim().  Start: the successive-SVD result (truncate_row).
+    Then `sweeps` rounds, each a left-to-right and a right-to-left pass over the
+    neighbour pairs (c, c+1).  At a pair, the sites outside it are isometries
+    (left-orthonormal left of c, right-orthonormal right of c+1), so the Y closest
+    to X in 2-norm with those sites fixed has the two-site tensor
+        Theta = <Y_<c| X_c X_{c+1} |Y_>c+1>   (overlap environments, exact),
+    and the best one of rank <= k at bond c+1 is its truncated SVD
+    (Eckart-Young).  Going right, Y_c = U (left-orthonormal) and Y_{c+1} = S V^T;
+    going left, Y_{c+1} = V^T and Y_c = U S.  No update increases ||X - Y||.
+
+    The singular-value record of a bond is that of its last update (the final
+    right-to-left pass).  Returns (tensors, log of the removed scale) like
+    truncate_row: Y_0 carries unit norm, the other sites are right-orthonormal."""
+    Y, logs = truncate_row(P, chi, Lx, Ly, r, env)
+    if Lx < 2 or sweeps <= 0:
+        return Y, logs
+    X = list(P)
+    # right environments of the start (Y_1.. right-orthonormal); log scales kept apart
+    R = [None] * (Lx + 1)
+    lR = np.zeros(Lx + 1)
+    R[Lx] = np.ones((1, 1))
+    for c in range(Lx - 1, 1, -1):
+        R[c], s = _rescaled(_right_overlap(R[c + 1], Y[c], X[c]))
+        lR[c] = lR[c + 1] + s
+    L = [None] * (Lx + 1)
+    lL = np.zeros(Lx + 1)
+    L[0] = np.ones((1, 1))
+
+    def theta(c):
+        T = np.einsum("ab,bsx,xtd,ed->aste", L[c], X[c], X[c + 1], R[c + 2])
+        a, _, _, e = T.shape
+        return T.reshape(a * 2, 2 * e), a, e
+
+    def split(c, going_right):
+        Th, a, e = theta(c)
+        U, S, Vh = np.linalg.svd(Th, full_matrices=False)
+        k = bond_dim(chi, Lx, Ly, r, c + 1)
+        if not S[0] > 0:
+            raise FloatingPointError("row %d: zero environment" % r)
+        if env is not None and not going_right:
+            tot = float(np.sum(S * S))
+            env.sv[(r, c + 1)] = S[:k] / math.sqrt(tot)
+            env.discarded[(r, c + 1)] = float(np.sum(S[k:] ** 2)) / tot
+        if going_right:
+            Y[c] = U[:, :k].reshape(a, 2, k)
+            Y[c + 1] = (S[:k, None] * Vh[:k]).reshape(k, 2, e)
+        else:
+            Y[c] = (U[:, :k] * S[None, :k]).reshape(a, 2, k)
+            Y[c + 1] = Vh[:k].reshape(k, 2, e)
+        return S[:k]
+
+    for _ in range(sweeps):
+        for c in range(Lx - 1):
+            split(c, True)
+            if c + 1 < Lx - 1:
+                L[c + 1], s = _rescaled(_left_overlap(L[c], Y[c], X[c]))
+                lL[c + 1] = lL[c] + s
+        for c in range(Lx - 2, -1, -1):
+            S = split(c, False)
+            if c > 0:
+                R[c + 1], s = _rescaled(_right_overlap(R[c + 2], Y[c + 1], X[c + 1]))
+                lR[c + 1] = lR[c + 2] + s
+    # Y_0 = U S: its norm is ||S_k||, the overlap scale is e^{lL[0] + lR[2]} = e^{lR[2]}
+    n0 = float(np.linalg.norm(S))
+    Y[0] = Y[0] / n0
+    return Y, float(lR[2] + math.log(n0))
+
+
+def build_env_variational(Jh, Jv, h, beta, chi, sweeps=1):
+    """Row environments compressed by two-site variational sweeps (truncate_row_variational)
+    instead of successive SVD; everything else as build_env."""
+    Jh, Jv, h, Lx, Ly = _check_lattice(Jh, Jv, h)
+    env = Env(Lx, Ly, float(beta), int(chi), Jh, Jv, h)
+    nxt = None
+    for r in range(Ly - 1, -1, -1):
+        P = apply_row_mpo(nxt, Jh, Jv, h, beta, r)
+        env.M[r], env.log_scale[r] = truncate_row_variational(P, chi, Lx, Ly, r, sweeps, env)
+        env.log_lambda[r] = env.log_lambda[r + 1] + env.log_scale[r]
+        nxt = env.M[r]
+    v = np.ones(1)
+    logv = 0.0
+    for c in range(Lx):
+        v = v @ (env.M[0][c][:, 0, :] + env.M[0][c][:, 1, :])
+        m = np.abs(v).max()
+        if m > 0:
+            v = v / m
+            logv += math.log(m)
+    env.logZ = env.log_lambda[0] + logv + math.log(v[0]) if v[0] > 0 else float("nan")
+    return env
