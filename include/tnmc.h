@@ -158,6 +158,22 @@ tnmc_status tnmc_build_env(const tnmc_lattice* lat, double beta, int chi, int pr
 tnmc_status tnmc_build_env_bond(const tnmc_lattice* lat, double beta, int chi, int precision_mask, void* stream,
                                 tnmc_env** out);
 
+/*
+ * The same environments with each row compressed by two-site variational sweeps
+ * (App. A names two-site variational compression beside successive SVD): a builder
+ * variant that defines another q.  T_chi starts from the successive-SVD result; each of
+ * `sweeps` rounds is a left-to-right and a right-to-left pass over the neighbour pairs
+ * (c, c+1), replacing the pair by the truncated SVD of the two-site tensor that is
+ * closest to the exact row D_r H_r V_r env_{r+1} with the other sites fixed (exact
+ * overlap environments; bond dims as successive SVD).  No update increases the
+ * 2-norm distance to the exact row.  sv / discarded (env_export) record each bond's last
+ * update.  sweeps in [0, 64] (0 is tnmc_build_env); always the dense (non-parity)
+ * builder.  Scratch: the builder's plus about (2 Lx) x 8 P^2 doubles.  Other arguments as
+ * tnmc_build_env.
+ */
+tnmc_status tnmc_build_env_variational(const tnmc_lattice* lat, double beta, int chi, int sweeps, int precision_mask,
+                                       void* stream, tnmc_env** out);
+
 tnmc_status tnmc_env_free(tnmc_env* env);
 
 /* Synchronises the env's build stream and fills `info`. */

@@ -51,6 +51,8 @@ SIGNATURES = {
     "tnmc_last_error": ([], ctypes.c_char_p),
     "tnmc_build_env": ([ctypes.POINTER(_Lattice), ctypes.c_double, _INT, _INT, _P, ctypes.POINTER(_P)], _INT),
     "tnmc_build_env_bond": ([ctypes.POINTER(_Lattice), ctypes.c_double, _INT, _INT, _P, ctypes.POINTER(_P)], _INT),
+    "tnmc_build_env_variational": ([ctypes.POINTER(_Lattice), ctypes.c_double, _INT, _INT, _INT, _P,
+                                    ctypes.POINTER(_P)], _INT),
     "tnmc_env_free": ([_P], _INT),
     "tnmc_env_info": ([_P, ctypes.POINTER(_Info)], _INT),
     "tnmc_env_export": ([_P, _P, _P, _P, _P, _P], _INT),
@@ -145,9 +147,11 @@ def _ptr(t):
 
 
 class Env:
-    """FP64-built row environments of one instance (owned by the library)."""
+    """FP64-built row environments of one instance (owned by the library).  gauge "spin"
+    or "bond" (App. A's bond basis); sweeps > 0 compresses each row by that many rounds of
+    two-site variational sweeps after successive SVD (spin basis only)."""
 
-    def __init__(self, Jh, Jv, h, beta, chi, precisions=("f64",), stream=None, gauge="spin"):
+    def __init__(self, Jh, Jv, h, beta, chi, precisions=("f64",), stream=None, gauge="spin", sweeps=0):
         h = np.ascontiguousarray(h, dtype=np.float64)
         Ly, Lx = h.shape
         Jh = np.ascontiguousarray(np.asarray(Jh, dtype=np.float64).reshape(Ly, max(Lx - 1, 0)))
@@ -160,8 +164,14 @@ class Env:
                        h.ctypes.data)
         out = ctypes.c_void_p()
         self._h = None
-        build = {"spin": lib().tnmc_build_env, "bond": lib().tnmc_build_env_bond}[gauge]
-        _check(build(ctypes.byref(lat), self.beta, self.chi, mask, _stream(stream), ctypes.byref(out)))
+        if sweeps:
+            if gauge != "spin":
+                raise ValueError("variational compression is built for the spin basis only")
+            _check(lib().tnmc_build_env_variational(ctypes.byref(lat), self.beta, self.chi, int(sweeps), mask,
+                                                    _stream(stream), ctypes.byref(out)))
+        else:
+            build = {"spin": lib().tnmc_build_env, "bond": lib().tnmc_build_env_bond}[gauge]
+            _check(build(ctypes.byref(lat), self.beta, self.chi, mask, _stream(stream), ctypes.byref(out)))
         self._h = out
 
     @classmethod
@@ -172,8 +182,9 @@ class Env:
         return self
 
     @classmethod
-    def from_instance(cls, inst, precisions=("f64",), chi=None, stream=None, gauge="spin"):
-        return cls(inst.Jh, inst.Jv, inst.h, inst.beta, inst.chi if chi is None else chi, precisions, stream, gauge)
+    def from_instance(cls, inst, precisions=("f64",), chi=None, stream=None, gauge="spin", sweeps=0):
+        return cls(inst.Jh, inst.Jv, inst.h, inst.beta, inst.chi if chi is None else chi, precisions, stream, gauge,
+                   sweeps)
 
     @property
     def handle(self):

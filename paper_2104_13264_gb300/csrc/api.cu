@@ -87,8 +87,8 @@ namespace {
 
 // Checks the arguments, allocates the environment's arena and uploads the
 // couplings; the tensors are written by a later builder launch.
-tnmc_status env_create(const tnmc_lattice* lat, double beta, int chi, int precision_mask, int gauge, cudaStream_t s,
-                       tnmc_env** out) {
+tnmc_status env_create(const tnmc_lattice* lat, double beta, int chi, int precision_mask, int gauge, int sweeps,
+                       cudaStream_t s, tnmc_env** out) {
   using namespace tnmc;
   *out = nullptr;
   CHECK_ARG(lat, "lattice must be non-null");
@@ -97,6 +97,8 @@ tnmc_status env_create(const tnmc_lattice* lat, double beta, int chi, int precis
   CHECK_ARG(chi >= 1 && chi <= kMaxChi, "chi = %d must be in [1, %d]", chi, kMaxChi);
   CHECK_ARG(gauge == 0 || chi <= kMaxChi / 2, "the bond basis samples from 2 chi bonds: chi = %d must be <= %d", chi,
             kMaxChi / 2);
+  CHECK_ARG(sweeps >= 0 && sweeps <= 64, "variational sweeps = %d must be in [0, 64]", sweeps);
+  CHECK_ARG(sweeps == 0 || gauge == 0, "variational compression is built for the spin basis only");
   CHECK_ARG(isfinite(beta) && beta >= 0.0, "beta must be finite and >= 0");
   CHECK_ARG(lat->h, "h must be non-null");
   CHECK_ARG(Lx == 1 || lat->Jh, "Jh must be non-null when Lx > 1");
@@ -166,9 +168,10 @@ tnmc_status env_create(const tnmc_lattice* lat, double beta, int chi, int precis
     bool zero_field = true;
     for (size_t i = 0; i < nh; ++i) zero_field = zero_field && (lat->h[i] == 0.0);
     const char* force = getenv("TNMC_DENSE_BUILDER");   // testing knob: the dense path on h = 0 lattices
-    d.z2 = zero_field && !(force && force[0] == '1') && gauge == 0;
+    d.z2 = zero_field && !(force && force[0] == '1') && gauge == 0 && sweeps == 0;
   }
   d.gauge = gauge;
+  d.sweeps = sweeps;
   d.Jh = reinterpret_cast<const double*>(base + oJh);
   d.Jv = reinterpret_cast<const double*>(base + oJv);
   d.h = reinterpret_cast<const double*>(base + oh);
@@ -233,19 +236,19 @@ extern "C" {
 
 const char* tnmc_last_error(void) { return g_err; }
 
-static tnmc_status build_env_gauge(const tnmc_lattice* lat, double beta, int chi, int precision_mask, int gauge,
-                                   void* stream, tnmc_env** out) {
+static tnmc_status build_env_variant(const tnmc_lattice* lat, double beta, int chi, int precision_mask, int gauge,
+                                     int sweeps, void* stream, tnmc_env** out) {
   using namespace tnmc;
   g_err[0] = 0;
   CHECK_ARG(lat && out, "lat and out must be non-null");
   *out = nullptr;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   tnmc_env* env = nullptr;
-  tnmc_status st = env_create(lat, beta, chi, precision_mask, gauge, s, &env);
+  tnmc_status st = env_create(lat, beta, chi, precision_mask, gauge, sweeps, s, &env);
   if (st != TNMC_OK) return st;
   const DeviceEnv& d = env->d;
   void* work = nullptr;
-  const size_t wbytes = tnmc_build_work_bytes(d.Lx, d.Ly, d.P);
+  const size_t wbytes = tnmc_build_work_bytes(d.Lx, d.Ly, d.P, d.sweeps);
   do {
     work = dev_alloc(env->alloc, wbytes, s);
     if (!work) {
@@ -271,12 +274,17 @@ static tnmc_status build_env_gauge(const tnmc_lattice* lat, double beta, int chi
 
 tnmc_status tnmc_build_env(const tnmc_lattice* lat, double beta, int chi, int precision_mask, void* stream,
                            tnmc_env** out) {
-  return build_env_gauge(lat, beta, chi, precision_mask, 0, stream, out);
+  return build_env_variant(lat, beta, chi, precision_mask, 0, 0, stream, out);
 }
 
 tnmc_status tnmc_build_env_bond(const tnmc_lattice* lat, double beta, int chi, int precision_mask, void* stream,
                                 tnmc_env** out) {
-  return build_env_gauge(lat, beta, chi, precision_mask, 1, stream, out);
+  return build_env_variant(lat, beta, chi, precision_mask, 1, 0, stream, out);
+}
+
+tnmc_status tnmc_build_env_variational(const tnmc_lattice* lat, double beta, int chi, int sweeps, int precision_mask,
+                                       void* stream, tnmc_env** out) {
+  return build_env_variant(lat, beta, chi, precision_mask, 0, sweeps, stream, out);
 }
 
 tnmc_status tnmc_build_env_batched(int n, const tnmc_lattice* lats, const double* beta, const int* chi,
@@ -293,7 +301,7 @@ tnmc_status tnmc_build_env_batched(int n, const tnmc_lattice* lats, const double
   tnmc_status st = TNMC_OK;
   size_t wtotal = 0;
   for (int i = 0; i < n && st == TNMC_OK; ++i) {
-    st = env_create(&lats[i], beta[i], chi[i], precision_mask, 0, s, &envs[i]);
+    st = env_create(&lats[i], beta[i], chi[i], precision_mask, 0, 0, s, &envs[i]);
     if (st != TNMC_OK) {
       char msg[512];
       snprintf(msg, sizeof msg, "instance %d: %s", i, g_err);
@@ -302,7 +310,7 @@ tnmc_status tnmc_build_env_batched(int n, const tnmc_lattice* lats, const double
     }
     const DeviceEnv& d = envs[i]->d;
     woff[i] = wtotal;
-    wtotal += align256(tnmc_build_work_bytes(d.Lx, d.Ly, d.P));
+    wtotal += align256(tnmc_build_work_bytes(d.Lx, d.Ly, d.P, d.sweeps));
   }
   const Allocator A = current_allocator();
   void* work = nullptr;

@@ -46,6 +46,8 @@ struct BuildArgs {
   int32_t* esz;   // [Ly][Lx+1] even-sector size of every bond (Z2 builder)
   int z2;         // parity-sector builder (all fields zero)
   int gauge;      // 1: bond basis (vertical bonds split as W = B T)
+  int sweeps;     // > 0: two-site variational rounds after successive SVD (dense builder)
+  double* vw;     // their scratch (after the Lx + 2 slots of `work`)
 };
 
 // The split W = B T of a vertical bond weight W[s][s'] = exp(beta J s s') (App. A): W has
@@ -263,7 +265,74 @@ __device__ void householder_qr(double* A, int m, int n, double* Q, double* Rout,
 // ---------------------------------------------------------------------------
 // 2. Left-to-right QR sweep.  Returns the accumulated log of removed scales.
 // ---------------------------------------------------------------------------
+// Bond basis: the upper factor T mixes the physical index, so the site tensors lose the
+// copy structure (physical spin == right horizontal copy) that qr_sweep factors block
+// by block.  Here each site is one (2 m) x Dr matrix, rows (left, physical), and its QR
+// gives a new bond of min(2 m, Dr).  Dims stay <= 2 max_bond <= P, so A and Q fit in
+// 2 P^2 doubles each and R in P^2.
+__device__ double qr_sweep_dense(const BuildArgs& a, Shared& sh) {
+  const int Lx = a.Lx, P = a.P;
+  const size_t slot_sz = (size_t)8 * P * P;
+  double logs = 0.0;
+  double* A = sh.W;
+  double* Q = sh.W + 2 * P * P;
+  double* Rb = sh.W + 4 * P * P;
+  double* tau = sh.W + 6 * P * P;
+  double* diag = tau + P;
+  for (int c = 0; c < Lx - 1; ++c) {
+    const int M = 2 * sh.dl[c];
+    const int Dr = sh.dr[c];
+    const int k = min(M, Dr);
+    const double* X = a.work + (size_t)sh.slot[c] * slot_sz;
+    double* Tn = a.work + (size_t)sh.slot[Lx] * slot_sz;   // new site c: [dl][2][k]
+    for (int idx = threadIdx.x; idx < M * Dr; idx += blockDim.x) {
+      const int l = idx / M, q = idx % M;   // column-major A[l*M + q]
+      A[idx] = X[(size_t)q * Dr + l];
+    }
+    __syncthreads();
+    householder_qr(A, M, Dr, Q, Rb, tau, diag);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < M * k; idx += blockDim.x) {
+      const int j = idx / M, q = idx % M;
+      Tn[(size_t)q * k + j] = Q[j * M + q];
+    }
+    double mx = 0.0;
+    for (int idx = threadIdx.x; idx < k * Dr; idx += blockDim.x) mx = fmax(mx, fabs(Rb[idx]));
+    mx = block_max(mx, sh.red);
+    if (!(mx > 0.0) || !isfinite(mx)) {
+      if (threadIdx.x == 0) set_status(a.status, TNMC_E_NUMERIC);
+      mx = 1.0;
+    }
+    logs += log(mx);
+    const double inv = 1.0 / mx;
+    // absorb R into site c+1: new[j][x'] = sum_{b >= j} R[j][b] old[b][x']
+    const double* O = a.work + (size_t)sh.slot[c + 1] * slot_sz;
+    double* Nn = a.work + (size_t)sh.slot[Lx + 1] * slot_sz;
+    const int ncol = 2 * sh.dr[c + 1];
+    for (int idx = threadIdx.x; idx < k * ncol; idx += blockDim.x) {
+      const int j = idx / ncol, col = idx % ncol;
+      double acc = 0.0;
+      for (int b = j; b < Dr; ++b) acc += Rb[j * Dr + b] * O[(size_t)b * ncol + col];
+      Nn[idx] = acc * inv;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int t = sh.slot[c];
+      sh.slot[c] = sh.slot[Lx];
+      sh.slot[Lx] = t;
+      t = sh.slot[c + 1];
+      sh.slot[c + 1] = sh.slot[Lx + 1];
+      sh.slot[Lx + 1] = t;
+      sh.dr[c] = k;
+      sh.dl[c + 1] = k;
+    }
+    __syncthreads();
+  }
+  return logs;
+}
+
 __device__ double qr_sweep(const BuildArgs& a, Shared& sh) {
+  if (a.gauge == 1) return qr_sweep_dense(a, sh);
   const int Lx = a.Lx, P = a.P;
   const size_t slot_sz = (size_t)8 * P * P;
   double logs = 0.0;
@@ -540,6 +609,309 @@ __device__ double svd_sweep(const BuildArgs& a, Shared& sh, int r) {
   return logs;
 }
 
+// ---------------------------------------------------------------------------
+// 4. Two-site variational compression (App. A names it beside successive SVD).
+//
+// X is the exact row (the MPO-MPS product, saved before the QR sweep), Y the
+// successive-SVD result in the slots.  Each round is a left-to-right and a
+// right-to-left pass over the pairs (c, c+1).  With the sites outside the pair
+// isometries, the closest Y to X has the two-site tensor
+//   Theta[(a,s),(t,b)] = sum Lenv[a][a'] X_c[a'][s][x] X_{c+1}[x][t][b'] Renv[b][b'],
+// and the best one of rank k at bond c+1 is its truncated SVD.  Going right,
+// Y_c = U (one-sided Jacobi on the rows of Theta^T gives u_j to working accuracy
+// however small s_j is) and Y_{c+1} = U^T Theta; going left, Y_{c+1} = V^T (Jacobi
+// on the rows of Theta) and Y_c = Theta V.  Overlap environments are rescaled by
+// their largest entry; the log of the scale of Renv[2] plus the norm of the final
+// Y_0 is the row's log-scale.  Scratch (a.vw): X store (Lx slots), T1, T2, Theta
+// (one slot each), Lenv[c] and Renv[c] (2 P^2 each, c <= Lx), log-scales of Renv, dims.
+// Sites left of a pair are untouched by a right-to-left pass until it reaches them,
+// so the Lenv[c] of the left-to-right pass serve it.
+// ---------------------------------------------------------------------------
+struct VarWork {
+  double* X;      // [Lx] slots
+  double* T1;
+  double* T2;
+  double* Th;
+  double* Lenv;   // [Lx + 1][2 P^2]
+  double* Renv;   // [Lx + 1][2 P^2]
+  double* lR;     // [Lx + 1]
+  int* xdl;       // [Lx] left / right dims of X_c
+  int* xdr;
+};
+
+__device__ inline VarWork var_work(const BuildArgs& a) {
+  const size_t slot_sz = (size_t)8 * a.P * a.P;
+  VarWork v;
+  v.X = a.vw;
+  v.T1 = v.X + (size_t)a.Lx * slot_sz;
+  v.T2 = v.T1 + slot_sz;
+  v.Th = v.T2 + slot_sz;
+  v.Lenv = v.Th + slot_sz;
+  v.Renv = v.Lenv + (size_t)(a.Lx + 1) * 2 * a.P * a.P;
+  v.lR = v.Renv + (size_t)(a.Lx + 1) * 2 * a.P * a.P;
+  v.xdl = reinterpret_cast<int*>(v.lR + a.Lx + 1);
+  v.xdr = v.xdl + a.Lx;
+  return v;
+}
+
+size_t var_work_doubles(int Lx, int P) {
+  const size_t slot_sz = (size_t)8 * P * P;
+  return (size_t)(Lx + 3) * slot_sz + (size_t)(Lx + 1) * 4 * P * P + (Lx + 1) + Lx;   // + 2 Lx ints
+}
+
+// The exact row X (slots as apply_row_mpo left them) into the X store.
+__device__ void var_save_x(const BuildArgs& a, Shared& sh) {
+  const VarWork v = var_work(a);
+  const size_t slot_sz = (size_t)8 * a.P * a.P;
+  for (int c = 0; c < a.Lx; ++c) {
+    const double* src = a.work + (size_t)sh.slot[c] * slot_sz;
+    double* dst = v.X + (size_t)c * slot_sz;
+    const int n = sh.dl[c] * 2 * sh.dr[c];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+    if (threadIdx.x == 0) {
+      v.xdl[c] = sh.dl[c];
+      v.xdr[c] = sh.dr[c];
+    }
+  }
+  __syncthreads();
+}
+
+// Renv_out[ay][ax] = sum_{t, by, bx} Y[ay][t][by] X[ax][t][bx] Renv_in[by][bx]; returns the
+// log of the largest entry, divided out.  tmp: [ax][t][by].
+__device__ double var_right_overlap(const BuildArgs& a, Shared& sh, const double* Y, int ay, int by, const double* X,
+                                    int ax, int bx, const double* Rin, double* tmp, double* Rout) {
+  for (int idx = threadIdx.x; idx < ax * 2 * by; idx += blockDim.x) {
+    const int b = idx % by, q = idx / by;   // q = (x, t)
+    double acc = 0.0;
+    for (int k = 0; k < bx; ++k) acc += X[(size_t)q * bx + k] * Rin[(size_t)b * bx + k];
+    tmp[idx] = acc;
+  }
+  __syncthreads();
+  double mx = 0.0;
+  for (int idx = threadIdx.x; idx < ay * ax; idx += blockDim.x) {
+    const int i = idx / ax, x = idx % ax;
+    double acc = 0.0;
+    for (int t = 0; t < 2; ++t)
+      for (int b = 0; b < by; ++b) acc += Y[((size_t)i * 2 + t) * by + b] * tmp[((size_t)x * 2 + t) * by + b];
+    Rout[idx] = acc;
+    mx = fmax(mx, fabs(acc));
+  }
+  mx = block_max(mx, sh.red);
+  if (!(mx > 0.0) || !isfinite(mx)) {
+    if (threadIdx.x == 0) set_status(a.status, TNMC_E_NUMERIC);
+    mx = 1.0;
+  }
+  const double inv = 1.0 / mx;
+  for (int idx = threadIdx.x; idx < ay * ax; idx += blockDim.x) Rout[idx] *= inv;
+  __syncthreads();
+  return log(mx);
+}
+
+// Theta of pair (c, c+1) into v.Th (m x n row-major, m = 2 ay, n = 2 by); T1 = Lenv X_c kept.
+__device__ void var_theta(const BuildArgs& a, const VarWork& v, int c, int ay, int by) {
+  const size_t slot_sz = (size_t)8 * a.P * a.P;
+  const double* Xc = v.X + (size_t)c * slot_sz;
+  const double* Xn = v.X + (size_t)(c + 1) * slot_sz;
+  const double* R = v.Renv + (size_t)(c + 2) * 2 * a.P * a.P;
+  const double* Le = v.Lenv + (size_t)c * 2 * a.P * a.P;
+  const int ax = v.xdl[c], xm = v.xdr[c], bx = v.xdr[c + 1];
+  // T1[ay][s][x] = sum_ax' Lenv[ay][ax'] X_c[ax'][s][x]
+  for (int idx = threadIdx.x; idx < ay * 2 * xm; idx += blockDim.x) {
+    const int i = idx / (2 * xm), q = idx % (2 * xm);
+    double acc = 0.0;
+    for (int k = 0; k < ax; ++k) acc += Le[(size_t)i * ax + k] * Xc[(size_t)k * 2 * xm + q];
+    v.T1[idx] = acc;
+  }
+  __syncthreads();
+  // T2[(ay,s)][t][bx] = sum_x T1[(ay,s)][x] X_{c+1}[x][t][bx]
+  for (int idx = threadIdx.x; idx < ay * 2 * 2 * bx; idx += blockDim.x) {
+    const int row = idx / (2 * bx), q = idx % (2 * bx);
+    double acc = 0.0;
+    for (int k = 0; k < xm; ++k) acc += v.T1[(size_t)row * xm + k] * Xn[(size_t)k * 2 * bx + q];
+    v.T2[idx] = acc;
+  }
+  __syncthreads();
+  // Theta[(ay,s)][(t,by)] = sum_bx T2[(ay,s)][t][bx] Renv[by][bx]
+  const int n = 2 * by;
+  for (int idx = threadIdx.x; idx < ay * 2 * n; idx += blockDim.x) {
+    const int row = idx / n, col = idx % n;
+    const int t = col / by, b = col % by;
+    double acc = 0.0;
+    for (int k = 0; k < bx; ++k) acc += v.T2[((size_t)row * 2 + t) * bx + k] * R[(size_t)b * bx + k];
+    v.Th[idx] = acc;
+  }
+  __syncthreads();
+}
+
+// Truncated SVD of Theta (m x n) to kk: one-sided Jacobi on the rows of Theta^T
+// (right) or of Theta (left).  Writes the new Y_c ([m/2][2][kk]) and Y_{c+1}
+// ([kk][2][n/2]); when `record`, the singular-value record of bond c+1.
+__device__ void var_split(const BuildArgs& a, Shared& sh, const VarWork& v, int r, int c, int m, int n, int kk,
+                          bool right, bool record, double* Yc, double* Yn) {
+  const int P = a.P;
+  const int rows = right ? n : m, len = right ? m : n;
+  const int ld = len + 1;
+  double* J = sh.W;
+  double* nrm = sh.W + 6 * P * P + 2 * P;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (kk > min(m, n) || rows > 128) {
+    if (threadIdx.x == 0) set_status(a.status, TNMC_E_NUMERIC);
+    return;
+  }
+  for (int idx = threadIdx.x; idx < m * n; idx += blockDim.x) {
+    const int i = idx / n, x = idx % n;
+    if (right) J[(size_t)x * ld + i] = v.Th[idx];
+    else J[(size_t)i * ld + x] = v.Th[idx];
+  }
+  __syncthreads();
+  if (!jacobi_rows(J, rows, len, ld, nrm, sh.flag) && threadIdx.x == 0) set_status(a.status, TNMC_E_NUMERIC);
+  for (int i = w; i < rows; i += kWarps) {
+    double s = 0.0;
+    for (int x = lane; x < len; x += 32) s += J[i * ld + x] * J[i * ld + x];
+    s = warp_sum(s);
+    if (lane == 0) nrm[i] = sqrt(s);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+    int rank = 0;
+    const double ni = nrm[i];
+    for (int j = 0; j < rows; ++j) {
+      const double nj = nrm[j];
+      rank += (nj > ni) || (nj == ni && j < i);
+    }
+    if (rank < kk) sh.sel[rank] = i;
+  }
+  __syncthreads();
+  const double smax = nrm[sh.sel[0]];
+  if (!(smax > 0.0) || !isfinite(smax)) {
+    if (threadIdx.x == 0) set_status(a.status, TNMC_E_NUMERIC);
+    return;
+  }
+  if (record) {
+    double tot = 0.0, dsc = 0.0;
+    for (int i = threadIdx.x; i < rows; i += blockDim.x) tot += nrm[i] * nrm[i];
+    tot = block_sum(tot, sh.red);
+    for (int j = threadIdx.x; j < rows; j += blockDim.x) {
+      int rank = 0;
+      for (int i = 0; i < rows; ++i) rank += (nrm[i] > nrm[j]) || (nrm[i] == nrm[j] && i < j);
+      if (rank >= kk) dsc += nrm[j] * nrm[j];
+    }
+    dsc = block_sum(dsc, sh.red);
+    double* svr = a.sv + ((size_t)r * (a.Lx + 1) + c + 1) * P;
+    for (int j = threadIdx.x; j < P; j += blockDim.x) svr[j] = (j < kk) ? nrm[sh.sel[j]] / sqrt(tot) : 0.0;
+    if (threadIdx.x == 0) a.disc[r * (a.Lx + 1) + c + 1] = dsc / tot;
+  }
+  // the isometry: kept rows normalised (rows at the rounding level stay zero)
+  double* iso = right ? v.T2 : Yn;   // right: U^T rows (kk x m) staged in T2; left: V^T = Y_{c+1}
+  for (int idx = threadIdx.x; idx < kk * len; idx += blockDim.x) {
+    const int j = idx / len, x = idx % len;
+    const int i = sh.sel[j];
+    const double nv = nrm[i];
+    iso[idx] = (nv > kNullRel * smax) ? J[i * ld + x] / nv : 0.0;
+  }
+  __syncthreads();
+  if (right) {
+    // Y_c[q][j] = u_j[q];  Y_{c+1}[j][x] = sum_q u_j[q] Theta[q][x]
+    for (int idx = threadIdx.x; idx < m * kk; idx += blockDim.x) {
+      const int q = idx / kk, j = idx % kk;
+      Yc[idx] = iso[(size_t)j * m + q];
+    }
+    for (int idx = threadIdx.x; idx < kk * n; idx += blockDim.x) {
+      const int j = idx / n, x = idx % n;
+      double acc = 0.0;
+      for (int q = 0; q < m; ++q) acc += iso[(size_t)j * m + q] * v.Th[(size_t)q * n + x];
+      Yn[idx] = acc;
+    }
+  } else {
+    // Y_c[q][j] = sum_x Theta[q][x] v_j[x]
+    for (int idx = threadIdx.x; idx < m * kk; idx += blockDim.x) {
+      const int q = idx / kk, j = idx % kk;
+      double acc = 0.0;
+      for (int x = 0; x < n; ++x) acc += v.Th[(size_t)q * n + x] * iso[(size_t)j * n + x];
+      Yc[idx] = acc;
+    }
+  }
+  __syncthreads();
+}
+
+// Returns the row's log-scale; Y_0 (unnormalised, norm = the removed scale's
+// remainder) and the right-orthonormal Y_1.. are left in the slots.
+__device__ double variational_sweeps(const BuildArgs& a, Shared& sh, int r) {
+  const int Lx = a.Lx, P = a.P;
+  const size_t slot_sz = (size_t)8 * P * P;
+  const size_t env_sz = (size_t)2 * P * P;
+  const VarWork v = var_work(a);
+  auto Yp = [&](int c) { return a.work + (size_t)sh.slot[c] * slot_sz; };
+  // right environments of the successive-SVD start
+  if (threadIdx.x == 0) {
+    v.Renv[(size_t)Lx * env_sz] = 1.0;
+    v.lR[Lx] = 0.0;
+  }
+  __syncthreads();
+  for (int c = Lx - 1; c >= 2; --c) {
+    const double l = var_right_overlap(a, sh, Yp(c), sh.dl[c], sh.dr[c], v.X + (size_t)c * slot_sz, v.xdl[c], v.xdr[c],
+                                       v.Renv + (size_t)(c + 1) * env_sz, v.T1, v.Renv + (size_t)c * env_sz);
+    if (threadIdx.x == 0) v.lR[c] = v.lR[c + 1] + l;
+    __syncthreads();
+  }
+  for (int sweep = 0; sweep < a.sweeps; ++sweep) {
+    if (threadIdx.x == 0) v.Lenv[0] = 1.0;
+    __syncthreads();
+    for (int c = 0; c < Lx - 1; ++c) {
+      const int ay = sh.dl[c], by = sh.dr[c + 1];
+      const int kk = bond_dim_dev(a.chi, Lx, a.Ly, r, c + 1);
+      var_theta(a, v, c, ay, by);
+      var_split(a, sh, v, r, c, 2 * ay, 2 * by, kk, true, false, Yp(c), Yp(c + 1));
+      if (threadIdx.x == 0) {
+        sh.dr[c] = kk;
+        sh.dl[c + 1] = kk;
+      }
+      __syncthreads();
+      if (c + 1 < Lx - 1) {
+        // Lenv[c+1][j][x] = sum_{a, s} Y_c[a][s][j] T1[a][s][x]  (T1 = Lenv[c] X_c, still in place)
+        const int xm = v.xdr[c];
+        const double* Yc = Yp(c);
+        double* Lo = v.Lenv + (size_t)(c + 1) * env_sz;
+        double mx = 0.0;
+        for (int idx = threadIdx.x; idx < kk * xm; idx += blockDim.x) {
+          const int j = idx / xm, x = idx % xm;
+          double acc = 0.0;
+          for (int q = 0; q < 2 * ay; ++q) acc += Yc[(size_t)q * kk + j] * v.T1[(size_t)q * xm + x];
+          Lo[idx] = acc;
+          mx = fmax(mx, fabs(acc));
+        }
+        mx = block_max(mx, sh.red);
+        if (!(mx > 0.0) || !isfinite(mx)) {
+          if (threadIdx.x == 0) set_status(a.status, TNMC_E_NUMERIC);
+          mx = 1.0;
+        }
+        const double inv = 1.0 / mx;
+        for (int idx = threadIdx.x; idx < kk * xm; idx += blockDim.x) Lo[idx] *= inv;
+        __syncthreads();
+      }
+    }
+    for (int c = Lx - 2; c >= 0; --c) {
+      const int ay = sh.dl[c], by = sh.dr[c + 1];
+      const int kk = bond_dim_dev(a.chi, Lx, a.Ly, r, c + 1);
+      var_theta(a, v, c, ay, by);
+      var_split(a, sh, v, r, c, 2 * ay, 2 * by, kk, false, true, Yp(c), Yp(c + 1));
+      if (threadIdx.x == 0) {
+        sh.dr[c] = kk;
+        sh.dl[c + 1] = kk;
+      }
+      __syncthreads();
+      if (c > 0) {
+        const double l = var_right_overlap(a, sh, Yp(c + 1), kk, sh.dr[c + 1], v.X + (size_t)(c + 1) * slot_sz,
+                                           v.xdl[c + 1], v.xdr[c + 1], v.Renv + (size_t)(c + 2) * env_sz, v.T1,
+                                           v.Renv + (size_t)(c + 1) * env_sz);
+        if (threadIdx.x == 0) v.lR[c + 1] = v.lR[c + 2] + l;
+        __syncthreads();
+      }
+    }
+  }
+  return v.lR[2];
+}
+
 __device__ void build_env_body(const BuildArgs& a, double* smem) {
   const int Lx = a.Lx, P = a.P;
   Shared sh;
@@ -555,8 +927,10 @@ __device__ void build_env_body(const BuildArgs& a, double* smem) {
 
   for (int r = a.Ly - 1; r >= 0; --r) {
     apply_row_mpo(a, sh, r);
+    if (a.sweeps > 0) var_save_x(a, sh);
     double logs = qr_sweep(a, sh);
     logs += svd_sweep(a, sh, r);
+    if (a.sweeps > 0 && Lx >= 2) logs = variational_sweeps(a, sh, r);
     // normalise site 0
     {
       const double* T0 = a.work + (size_t)sh.slot[0] * slot_sz;
@@ -1225,9 +1599,10 @@ tnmc_status tnmc_launch_bond_sampling(tnmc_env* env, cudaStream_t stream) {
   return TNMC_OK;
 }
 
-size_t tnmc_build_work_bytes(int Lx, int Ly, int P) {
+size_t tnmc_build_work_bytes(int Lx, int Ly, int P, int sweeps) {
   (void)Ly;
-  return (size_t)(Lx + 2) * 8 * P * P * sizeof(double);
+  const size_t base = (size_t)(Lx + 2) * 8 * P * P * sizeof(double);
+  return sweeps > 0 ? base + tnmc::var_work_doubles(Lx, P) * sizeof(double) : base;
 }
 
 static size_t build_smem_bytes(int Lx, int P) {
@@ -1257,13 +1632,15 @@ static tnmc::BuildArgs make_build_args(tnmc_env* env, void* work) {
   a.esz = env->esz;
   a.z2 = d.z2;
   a.gauge = d.gauge;
+  a.sweeps = d.sweeps;
+  a.vw = d.sweeps > 0 ? a.work + (size_t)(d.Lx + 2) * 8 * d.P * d.P : nullptr;
   return a;
 }
 
 tnmc_status tnmc_launch_build(tnmc_env* env, cudaStream_t stream, void* work, size_t work_bytes) {
   using namespace tnmc;
   const DeviceEnv& d = env->d;
-  if (work_bytes < tnmc_build_work_bytes(d.Lx, d.Ly, d.P)) {
+  if (work_bytes < tnmc_build_work_bytes(d.Lx, d.Ly, d.P, d.sweeps)) {
     tnmc_set_error("build scratch too small");
     return TNMC_E_INVALID_ARG;
   }

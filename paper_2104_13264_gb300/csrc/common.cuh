@@ -30,6 +30,7 @@ struct DeviceEnv {
   int integer_couplings;
   int z2;             // 1 when every field is zero: the builder uses parity sectors
   int gauge;          // 0: spin basis; 1: bond basis (rows sampled from the untruncated 2 chi MPS)
+  int sweeps;         // two-site variational rounds after successive SVD (0: successive SVD only)
   const double* Jh;   // device copies of the couplings
   const double* Jv;
   const double* h;
@@ -177,7 +178,7 @@ tnmc_status tnmc_launch_build(tnmc_env* env, cudaStream_t stream, void* work, si
 tnmc_status tnmc_launch_build_batched(tnmc_env* const* envs, int n, void* work, const size_t* work_offsets,
                                       void* args_dev, cudaStream_t stream);
 size_t tnmc_build_args_bytes();
-size_t tnmc_build_work_bytes(int Lx, int Ly, int P);
+size_t tnmc_build_work_bytes(int Lx, int Ly, int P, int sweeps);
 tnmc_status tnmc_launch_derive(tnmc_env* env, int precision_mask, cudaStream_t stream);
 tnmc_status tnmc_launch_bond_sampling(tnmc_env* env, cudaStream_t stream);
 tnmc_status tnmc_launch_sample(const tnmc_env* env, int precision, int64_t B, uint64_t seed,
