@@ -452,6 +452,82 @@ tnmc_status tnmc_metropolis_batched(tnmc_batch* plan, int8_t* chain_spins, doubl
  */
 tnmc_status tnmc_link_overlap_batched(tnmc_batch* plan, const int8_t* chain_spins, double* overlap, void* stream);
 
+/* ------------------------------------------------------------------------------------
+ * Three-dimensional lattices (Sec. 3D; App. A, three-dimensional paragraph and Figs.
+ * peps-cutoff2, peps-cutoff).
+ *
+ * Lattice Lz x Ly x Lx, open boundaries, site (z, y, x), index (z*Ly + y)*Lx + x; layer
+ * z = 0 is sampled first, each layer in raster order.  Spins int8 [sample][Lz][Ly][Lx].
+ * H = -sum h s - sum J s s with Jx [Lz][Ly][Lx-1] bond (z,y,x)-(z,y,x+1),
+ * Jy [Lz][Ly-1][Lx] bond (z,y,x)-(z,y+1,x), Jz [Lz-1][Ly][Lx] bond (z,y,x)-(z+1,y,x),
+ * h [Lz][Ly][Lx]; row-major FP64 host arrays.
+ * ---------------------------------------------------------------------------------- */
+typedef struct {
+  int Lx, Ly, Lz;
+  const double* Jx;
+  const double* Jy;
+  const double* Jz;
+  const double* h;
+} tnmc_lattice3d;
+
+typedef struct tnmc3d_env tnmc3d_env;
+
+/*
+ * Layer environments: PEPS of bond D over the spins of each layer, bottom-up,
+ *   env_{Lz-1} = the exact weight of the last layer,
+ *   env_z = T_D[ D_z H_z V_z env_{z+1} ]
+ * (V_z: the sum over layer z+1 through exp(beta Jz s s'); D_z: fields; H_z: the in-layer
+ * bonds as copy structure, each doubling its bond).  T_D is the paper's renormalisation
+ * (Fig. peps-cutoff2): every column is read as an MPS with the column's vertical bonds as
+ * MPS bonds and the spin and the two horizontal bonds as physical index, compressed by
+ * successive SVD keeping min(D, rank bound) values per bond; then every row likewise
+ * along its horizontal bonds.  `chi` is the boundary-MPS bond used by the sampler.
+ * The build is synchronous.  Limits: Lx, Ly <= 64; D <= 8; chi <= 32; D chi <= 64.
+ * Errors: TNMC_E_INVALID_ARG (arguments), TNMC_E_NOMEM, TNMC_E_CUDA; numerical trouble
+ * (a zero column, a Jacobi SVD that does not converge) sets the env's status word.
+ */
+tnmc_status tnmc3d_build_env(const tnmc_lattice3d* lat, double beta, int D, int chi, void* stream, tnmc3d_env** out);
+tnmc_status tnmc3d_env_free(tnmc3d_env* env);
+/* Synchronises and reads the status word (0 = clean; else a tnmc_status). */
+tnmc_status tnmc3d_env_status(const tnmc3d_env* env, int32_t* status);
+/*
+ * Host copies (synchronous; any pointer may be NULL): tensors [Lz][Ly][Lx][2][D][D][D][D]
+ * A[s][u][l][d][r] (u: bond to row y-1, l: to column x-1, d: to row y+1, r: to column
+ * x+1; zero outside the dims), dims [Lz][Ly][Lx][4] = (du, dl, dd, dr), log_scale [Lz]
+ * (log of the factor removed while compressing layer z).
+ */
+tnmc_status tnmc3d_env_export(const tnmc3d_env* env, double* tensors, int32_t* dims, double* log_scale);
+
+/*
+ * Draw B proposals from the 3D q.  Layer z is sampled with the spins of layer z-1 as
+ * fields f(s) = exp(beta Jz s_up s); row y of the layer from the sandwich of Top_y (rows
+ * < y at their drawn spins, an MPS of bond chi over the row's upper bonds) x row y x
+ * Bot_y (rows > y summed, an MPS of bond chi over its lower bonds), both rebuilt for
+ * every sample by successive SVD (Bot_y = T_chi[S_{y+1} Bot_{y+1}], S = sum_s A f;
+ * Top_{y+1} = T_chi[Top_y F_y], F = A f at the drawn spins).  Site conditionals are
+ * clamped at zero and normalised; sample b (index sample_offset + b) draws site i with
+ * the Philox word of (i, sample) as in two dimensions.  Also returns the exact log q of
+ * each draw (sum of the logs of the probabilities used) and its energy (FP64).  One
+ * thread per sample; the samples' scratch (about 8 (L^2 chi^2 D + L (D chi)^2 D) bytes
+ * each) is taken from the env's allocator in chunks of at most 4 GiB.
+ * precision  TNMC_F64 or TNMC_F32 (the FP32 copy of the environment, FP32 arithmetic)
+ * spins      device int8 [B][Lz][Ly][Lx] (output); logq, energy device double [B];
+ * flags      device int32 [B] or NULL (TNMC_FLAG_NUMERIC: a site drawn at p = 1/2).
+ */
+tnmc_status tnmc3d_sample(const tnmc3d_env* env, int precision, int64_t B, uint64_t seed, uint64_t sample_offset,
+                          int8_t* spins, double* logq, double* energy, int32_t* flags, void* stream);
+/* Forced evaluation: log q and energy of given configurations (same arithmetic). */
+tnmc_status tnmc3d_logq(const tnmc3d_env* env, int precision, int64_t B, const int8_t* spins, double* logq,
+                        double* energy, int32_t* flags, void* stream);
+/* Random +-1 start of C chains (counter as tnmc_init_chains) and their forced log q, energy. */
+tnmc_status tnmc3d_init_chains(const tnmc3d_env* env, int precision, int64_t C, uint64_t seed, int8_t* chain_spins,
+                               double* chain_logq, double* chain_energy, void* stream);
+/* The MH scan of tnmc_mh_step on 3D configurations (n = Lz Ly Lx spins each). */
+tnmc_status tnmc3d_mh_step(const tnmc3d_env* env, int64_t C, int64_t T, const int8_t* prop_spins,
+                           const double* prop_logq, const double* prop_energy, int8_t* chain_spins,
+                           double* chain_logq, double* chain_energy, uint64_t seed, uint64_t step_offset,
+                           uint8_t* accepted, int64_t* n_accepted, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

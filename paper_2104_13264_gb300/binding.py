@@ -84,6 +84,22 @@ SIGNATURES = {
     "tnmc_link_overlap_batched": ([_P, _P, _P, _P], _INT),
 }
 
+class _Lattice3D(ctypes.Structure):
+    _fields_ = [("Lx", ctypes.c_int), ("Ly", ctypes.c_int), ("Lz", ctypes.c_int), ("Jx", ctypes.c_void_p),
+                ("Jy", ctypes.c_void_p), ("Jz", ctypes.c_void_p), ("h", ctypes.c_void_p)]
+
+
+SIGNATURES.update({
+    "tnmc3d_build_env": ([ctypes.POINTER(_Lattice3D), ctypes.c_double, _INT, _INT, _P, ctypes.POINTER(_P)], _INT),
+    "tnmc3d_env_free": ([_P], _INT),
+    "tnmc3d_env_status": ([_P, ctypes.POINTER(ctypes.c_int32)], _INT),
+    "tnmc3d_env_export": ([_P, _P, _P, _P], _INT),
+    "tnmc3d_sample": ([_P, _INT, _I64, _U64, _U64, _P, _P, _P, _P, _P], _INT),
+    "tnmc3d_logq": ([_P, _INT, _I64, _P, _P, _P, _P, _P], _INT),
+    "tnmc3d_init_chains": ([_P, _INT, _I64, _U64, _P, _P, _P, _P], _INT),
+    "tnmc3d_mh_step": ([_P, _I64, _I64, _P, _P, _P, _P, _P, _P, _U64, _U64, _P, _P, _P], _INT),
+})
+
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 _hooks = None   # keeps the ctypes callbacks alive while the library may call them
@@ -481,3 +497,113 @@ class Batch:
             self.free()
         except Exception:
             pass
+
+
+# ---- three-dimensional lattices (Sec. 3D) ----
+
+class Env3D:
+    """Layer environments of a cubic-lattice instance (PEPS of bond D; the sampler's boundary
+    MPS have bond chi), built by tnmc3d_build_env."""
+
+    def __init__(self, Jx, Jy, Jz, h, beta, D, chi, stream=None):
+        h = np.ascontiguousarray(h, dtype=np.float64)
+        Lz, Ly, Lx = h.shape
+        Jx = np.ascontiguousarray(np.asarray(Jx, dtype=np.float64).reshape(Lz, Ly, max(Lx - 1, 0)))
+        Jy = np.ascontiguousarray(np.asarray(Jy, dtype=np.float64).reshape(Lz, max(Ly - 1, 0), Lx))
+        Jz = np.ascontiguousarray(np.asarray(Jz, dtype=np.float64).reshape(max(Lz - 1, 0), Ly, Lx))
+        self.Lz, self.Ly, self.Lx = Lz, Ly, Lx
+        self.beta, self.D, self.chi = float(beta), int(D), int(chi)
+        lat = _Lattice3D(Lx, Ly, Lz, Jx.ctypes.data if Jx.size else None, Jy.ctypes.data if Jy.size else None,
+                         Jz.ctypes.data if Jz.size else None, h.ctypes.data)
+        out = ctypes.c_void_p()
+        self._h = None
+        _check(lib().tnmc3d_build_env(ctypes.byref(lat), self.beta, self.D, self.chi, _stream(stream),
+                                      ctypes.byref(out)))
+        self._h = out
+
+    @classmethod
+    def from_instance(cls, inst, D=None, chi=None, stream=None):
+        return cls(inst.Jx, inst.Jy, inst.Jz, inst.h, inst.beta, inst.D if D is None else D,
+                   inst.chi if chi is None else chi, stream)
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def n(self):
+        return self.Lz * self.Ly * self.Lx
+
+    def export(self):
+        """Host copies: tensors [Lz, Ly, Lx, 2, D, D, D, D], dims [Lz, Ly, Lx, 4], log_scale [Lz]."""
+        D = self.D
+        T = np.zeros((self.Lz, self.Ly, self.Lx, 2, D, D, D, D))
+        dims = np.zeros((self.Lz, self.Ly, self.Lx, 4), dtype=np.int32)
+        ls = np.zeros(self.Lz)
+        _check(lib().tnmc3d_env_export(self._h, T.ctypes.data, dims.ctypes.data, ls.ctypes.data))
+        return {"tensors": T, "dims": dims, "log_scale": ls}
+
+    def status(self):
+        s = ctypes.c_int32()
+        _check(lib().tnmc3d_env_status(self._h, ctypes.byref(s)))
+        return s.value
+
+    def free(self):
+        if self._h is not None and self._h.value:
+            lib().tnmc3d_env_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def sample3d(env, B, seed=0, sample_offset=0, precision="f64", stream=None):
+    """Draw B proposals on a cubic lattice: (spins int8 [B,Lz,Ly,Lx], logq, energy, flags) on cuda."""
+    import torch
+    dev = torch.device("cuda")
+    sp = torch.empty((B, env.Lz, env.Ly, env.Lx), dtype=torch.int8, device=dev)
+    lq = torch.empty(B, dtype=torch.float64, device=dev)
+    E = torch.empty(B, dtype=torch.float64, device=dev)
+    fl = torch.empty(B, dtype=torch.int32, device=dev)
+    _check(lib().tnmc3d_sample(env.handle, PRECISIONS[precision], B, seed, sample_offset, _ptr(sp), _ptr(lq), _ptr(E),
+                               _ptr(fl), _stream(stream)))
+    return sp, lq, E, fl
+
+
+def logq3d(env, spins, precision="f64", stream=None):
+    """Forced log q and energy of cubic-lattice configurations (int8 cuda tensor [B,Lz,Ly,Lx])."""
+    import torch
+    spins = spins.contiguous()
+    B = spins.shape[0]
+    lq = torch.empty(B, dtype=torch.float64, device=spins.device)
+    E = torch.empty(B, dtype=torch.float64, device=spins.device)
+    fl = torch.empty(B, dtype=torch.int32, device=spins.device)
+    _check(lib().tnmc3d_logq(env.handle, PRECISIONS[precision], B, _ptr(spins), _ptr(lq), _ptr(E), _ptr(fl),
+                             _stream(stream)))
+    return lq, E, fl
+
+
+def init_chains3d(env, C, seed=0, precision="f64", stream=None):
+    import torch
+    dev = torch.device("cuda")
+    sp = torch.empty((C, env.Lz, env.Ly, env.Lx), dtype=torch.int8, device=dev)
+    lq = torch.empty(C, dtype=torch.float64, device=dev)
+    E = torch.empty(C, dtype=torch.float64, device=dev)
+    _check(lib().tnmc3d_init_chains(env.handle, PRECISIONS[precision], C, seed, _ptr(sp), _ptr(lq), _ptr(E),
+                                    _stream(stream)))
+    return sp, lq, E
+
+
+def mh_step3d(env, C, T, prop, chain, seed=0, step_offset=0, accepted=None, n_accepted=None, stream=None):
+    """MH scan on cubic-lattice chains; as mh_step."""
+    import torch
+    ps, plq, pE = prop
+    cs, clq, cE = chain
+    if accepted is None:
+        accepted = torch.empty(C * T, dtype=torch.uint8, device=plq.device)
+    _check(lib().tnmc3d_mh_step(env.handle, C, T, _ptr(ps), _ptr(plq), _ptr(pE), _ptr(cs), _ptr(clq), _ptr(cE), seed,
+                                step_offset, _ptr(accepted), _ptr(n_accepted), _stream(stream)))
+    return accepted

@@ -180,6 +180,11 @@ tnmc_status tnmc_launch_build_batched(tnmc_env* const* envs, int n, void* work, 
 size_t tnmc_build_args_bytes();
 size_t tnmc_build_work_bytes(int Lx, int Ly, int P, int sweeps);
 tnmc_status tnmc_launch_derive(tnmc_env* env, int precision_mask, cudaStream_t stream);
+tnmc_status tnmc_launch_mh_core(int64_t n, double beta, const tnmc::Allocator& alloc, int64_t C, int64_t T,
+                                const int8_t* prop_spins, const double* prop_logq, const double* prop_energy,
+                                int8_t* chain_spins, double* chain_logq, double* chain_energy, uint64_t seed,
+                                uint64_t step_offset, uint8_t* accepted, int64_t* n_accepted, cudaStream_t stream);
+tnmc_status tnmc_launch_init_bits_core(int64_t n, int64_t C, uint64_t seed, int8_t* spins, cudaStream_t stream);
 tnmc_status tnmc_launch_bond_sampling(tnmc_env* env, cudaStream_t stream);
 tnmc_status tnmc_launch_sample(const tnmc_env* env, int precision, int64_t B, uint64_t seed,
                                uint64_t sample_offset, const int8_t* spins_in, int8_t* spins_out,

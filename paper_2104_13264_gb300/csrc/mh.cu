@@ -74,37 +74,48 @@ __global__ void init_bits_kernel(int64_t C, int64_t n, uint64_t seed, int8_t* sp
 }  // namespace
 }  // namespace tnmc
 
-tnmc_status tnmc_launch_mh(const tnmc_env* env, int64_t C, int64_t T, const int8_t* prop_spins,
-                           const double* prop_logq, const double* prop_energy, int8_t* chain_spins,
-                           double* chain_logq, double* chain_energy, uint64_t seed, uint64_t step_offset,
-                           uint8_t* accepted, int64_t* n_accepted, cudaStream_t stream) {
+tnmc_status tnmc_launch_mh_core(int64_t n, double beta, const tnmc::Allocator& alloc, int64_t C, int64_t T,
+                                const int8_t* prop_spins, const double* prop_logq, const double* prop_energy,
+                                int8_t* chain_spins, double* chain_logq, double* chain_energy, uint64_t seed,
+                                uint64_t step_offset, uint8_t* accepted, int64_t* n_accepted, cudaStream_t stream) {
   using namespace tnmc;
   if (C == 0 || T == 0) return TNMC_OK;
-  const int64_t n = (int64_t)env->d.Lx * env->d.Ly;
-  int64_t* last = static_cast<int64_t*>(dev_alloc(env->alloc, C * sizeof(int64_t), stream));
+  int64_t* last = static_cast<int64_t*>(dev_alloc(alloc, C * sizeof(int64_t), stream));
   if (!last) {
     tnmc_set_error("cannot allocate %zu bytes for the MH scan", (size_t)C * sizeof(int64_t));
     return TNMC_E_NOMEM;
   }
   const int threads = 128;
   const int64_t blocks = (C + threads - 1) / threads;
-  mh_scan_kernel<<<(unsigned)blocks, threads, 0, stream>>>(C, T, env->d.beta, prop_logq, prop_energy, chain_logq,
+  mh_scan_kernel<<<(unsigned)blocks, threads, 0, stream>>>(C, T, beta, prop_logq, prop_energy, chain_logq,
                                                            chain_energy, seed, step_offset, accepted, last,
                                                            n_accepted);
   TNMC_CUDA_TRY(cudaGetLastError());
   const int64_t cb = C < 65535 ? C : 65535;
   mh_copy_kernel<<<(unsigned)cb, 256, 0, stream>>>(C, n, last, prop_spins, chain_spins);
   TNMC_CUDA_TRY(cudaGetLastError());
-  dev_free(env->alloc, last, C * sizeof(int64_t), stream);
+  dev_free(alloc, last, C * sizeof(int64_t), stream);
+  return TNMC_OK;
+}
+
+tnmc_status tnmc_launch_mh(const tnmc_env* env, int64_t C, int64_t T, const int8_t* prop_spins,
+                           const double* prop_logq, const double* prop_energy, int8_t* chain_spins,
+                           double* chain_logq, double* chain_energy, uint64_t seed, uint64_t step_offset,
+                           uint8_t* accepted, int64_t* n_accepted, cudaStream_t stream) {
+  return tnmc_launch_mh_core((int64_t)env->d.Lx * env->d.Ly, env->d.beta, env->alloc, C, T, prop_spins, prop_logq,
+                             prop_energy, chain_spins, chain_logq, chain_energy, seed, step_offset, accepted,
+                             n_accepted, stream);
+}
+
+tnmc_status tnmc_launch_init_bits_core(int64_t n, int64_t C, uint64_t seed, int8_t* spins, cudaStream_t stream) {
+  using namespace tnmc;
+  if (C == 0) return TNMC_OK;
+  init_bits_kernel<<<1024, 256, 0, stream>>>(C, n, seed, spins);
+  TNMC_CUDA_TRY(cudaGetLastError());
   return TNMC_OK;
 }
 
 tnmc_status tnmc_launch_init_bits(const tnmc_env* env, int64_t C, uint64_t seed, int8_t* spins,
                                   cudaStream_t stream) {
-  using namespace tnmc;
-  if (C == 0) return TNMC_OK;
-  const int64_t n = (int64_t)env->d.Lx * env->d.Ly;
-  init_bits_kernel<<<1024, 256, 0, stream>>>(C, n, seed, spins);
-  TNMC_CUDA_TRY(cudaGetLastError());
-  return TNMC_OK;
+  return tnmc_launch_init_bits_core((int64_t)env->d.Lx * env->d.Ly, C, seed, spins, stream);
 }

@@ -151,3 +151,46 @@ def random_tensors(shapes, seed=0, positive=True):
         x = rng.standard_normal(shp)
         out.append(np.abs(x) + 0.1 if positive else x)
     return out
+
+
+@dataclass
+class Instance3D:
+    """A cubic-lattice instance: Jx [Lz, Ly, Lx-1], Jy [Lz, Ly-1, Lx], Jz [Lz-1, Ly, Lx],
+    h [Lz, Ly, Lx]; environment bond D and boundary-MPS bond chi (Sec. 3D)."""
+    name: str
+    Jx: np.ndarray
+    Jy: np.ndarray
+    Jz: np.ndarray
+    h: np.ndarray
+    beta: float
+    D: int
+    chi: int
+
+    @property
+    def shape(self):
+        return self.h.shape
+
+
+def cubic_uniform(L, beta, D, chi, J=1.0, hfield=0.0, name="cubic"):
+    """Uniform L^3 lattice with open boundaries: J > 0 ferromagnet, J < 0 antiferromagnet
+    (Sec. 3D: the ferromagnet, and the antiferromagnet in a field h = 3)."""
+    Lz = Ly = Lx = int(L)
+    return Instance3D(name, np.full((Lz, Ly, Lx - 1), float(J)), np.full((Lz, Ly - 1, Lx), float(J)),
+                      np.full((Lz - 1, Ly, Lx), float(J)), np.full((Lz, Ly, Lx), float(hfield)), float(beta), int(D),
+                      int(chi))
+
+
+def cubic_ferromagnet(L=16, T=4.6, D=2, chi=2):
+    return cubic_uniform(L, 1.0 / T, D, chi, J=1.0, name="ferro3d")
+
+
+def cubic_antiferromagnet(L=16, T=4.0, D=2, chi=2, hfield=3.0):
+    return cubic_uniform(L, 1.0 / T, D, chi, J=-1.0, hfield=hfield, name="antiferro3d_h3")
+
+
+def cubic_random(Lz, Ly, Lx, beta, D, chi, seed=0, hscale=0.3):
+    """Gaussian couplings and fields on an Lz x Ly x Lx box (parity cases)."""
+    g = np.random.default_rng(seed)
+    return Instance3D("random3d", g.standard_normal((Lz, Ly, Lx - 1)), g.standard_normal((Lz, Ly - 1, Lx)),
+                      g.standard_normal((Lz - 1, Ly, Lx)), hscale * g.standard_normal((Lz, Ly, Lx)), float(beta),
+                      int(D), int(chi))

@@ -14,7 +14,7 @@ def declared_symbols():
         if f.endswith(".h"):
             txt = open(os.path.join(ROOT, "include", f)).read()
             txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-            names |= set(re.findall(r"\b(tnmc_[a-z0-9_]+)\s*\(", txt))
+            names |= set(re.findall(r"\b(tnmc(?:3d)?_[a-z0-9_]+)\s*\(", txt))
     return sorted(names)
 
 
