@@ -55,6 +55,11 @@ typedef enum {
 /* Arithmetic of the sampler copy of the environment (the builder is always FP64). */
 typedef enum { TNMC_F64 = 0, TNMC_F32 = 1, TNMC_BF16 = 2 } tnmc_precision;
 
+/* Site order of the samplers (defines q; App. A's labelling of the sites is not fixed by
+ * the text).  Raster: every row left to right.  Snake: even rows left to right, odd rows
+ * right to left. */
+typedef enum { TNMC_ORDER_RASTER = 0, TNMC_ORDER_SNAKE = 1 } tnmc_order;
+
 /* Per-sample flag bits. */
 #define TNMC_FLAG_NUMERIC 1
 
@@ -175,6 +180,19 @@ tnmc_status tnmc_build_env_variational(const tnmc_lattice* lat, double beta, int
                                        void* stream, tnmc_env** out);
 
 tnmc_status tnmc_env_free(tnmc_env* env);
+
+/*
+ * Site order of every later sample / logq / init_chains / metropolis call on this env (and
+ * of batch plans created afterwards), TNMC_ORDER_RASTER (default) or TNMC_ORDER_SNAKE.  The
+ * environments do not depend on the order.  In snake order an odd row r is drawn from
+ * c = Lx-1 down to 0: a forward sweep V_{c+1} = sum_s f_c(s) V_c M_c[:, s, :] (sites < c
+ * summed) is stored, then w(s) = f_c(s) <V_c M_c[:, s, :], Lambda'_{c+1}> with Lambda' the
+ * drawn sites > c; draws, log q and energy otherwise as tnmc_sample (site r*Lx + c keeps its
+ * Philox counter).  The BF16 tensor-core sampler and tnmc_logq_backward support raster
+ * order only and return TNMC_E_UNSUPPORTED.  Not synchronised with work in flight: call it
+ * between launches.
+ */
+tnmc_status tnmc_env_set_order(tnmc_env* env, int order);
 
 /* Synchronises the env's build stream and fills `info`. */
 tnmc_status tnmc_env_info(const tnmc_env* env, tnmc_env_info_t* info);

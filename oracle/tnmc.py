@@ -58,6 +58,7 @@ class Env:
         self.discarded = {}             # (r, c) -> discarded squared weight fraction
         self.logZ = float("nan")
         self.Mr = None                  # optional Mr[r][c][u]: right-sweep tensors (env_bf16)
+        self.order = "raster"           # site order: "raster", or "snake" (odd rows right to left)
 
 
 def _check_lattice(Jh, Jv, h):
@@ -242,10 +243,18 @@ def run(env, B, seed=0, sample_offset=0, forced=None, keep=False, samples=None):
     else:
         samples = np.asarray(samples, dtype=np.uint64)
     record = []
+    snake = getattr(env, "order", "raster") == "snake"
+    if snake and (keep or env.Mr is not None):
+        raise NotImplementedError("snake order: no gradient record and no field-combined right tensors")
     with np.errstate(divide="ignore", invalid="ignore", over="ignore"):
         for r in range(Ly):
-            M = env.M[r]
             f = row_fields(env, spins, r)
+            # the row in sampling order: row r runs right to left in snake order when r is odd;
+            # the reversed row is the same MPS read backwards (site tensors with their bonds swapped)
+            cols = list(range(Lx - 1, -1, -1)) if (snake and r % 2 == 1) else list(range(Lx))
+            rev = cols[0] != 0
+            M = [env.M[r][c].transpose(2, 1, 0) if rev else env.M[r][c] for c in cols]
+            f = f[:, cols, :]
             R = [None] * (Lx + 1)
             R[Lx] = np.ones((B, 1))
             up = (spins[:, r - 1, :] > 0).astype(np.int64) if r > 0 else np.zeros((B, Lx), dtype=np.int64)
@@ -269,18 +278,19 @@ def run(env, B, seed=0, sample_offset=0, forced=None, keep=False, samples=None):
                 bad = ~(tot > 0) | ~np.isfinite(tot)
                 pplus = np.where(bad, 0.5, w[:, 1] / tot)
                 pminus = np.where(bad, 0.5, w[:, 0] / tot)
+                col = cols[c]
                 if forced is None:
-                    x = philox.draw_words(seed, r * Lx + c, samples)
+                    x = philox.draw_words(seed, r * Lx + col, samples)
                     plus = threshold_plus(pplus, x)
-                    spins[:, r, c] = np.where(plus, 1, -1)
+                    spins[:, r, col] = np.where(plus, 1, -1)
                 else:
-                    plus = spins[:, r, c] > 0
+                    plus = spins[:, r, col] > 0
                 logq += np.log(np.where(plus, pplus, pminus))
                 flags |= np.where(bad, F_BAD, 0).astype(np.int32)
                 idx = plus.astype(np.int64)
                 Lam[c + 1] = _pow2_normalize(U[np.arange(B), idx, :] * f[np.arange(B), c, idx][:, None])
             if keep:
-                record.append((f, R, Lam, wraw))
+                record.append((row_fields(env, spins, r), R, Lam, wraw))
     E = energy(env.Jh, env.Jv, env.h, spins)
     if keep:
         return spins, logq, E, flags, record

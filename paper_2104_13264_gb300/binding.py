@@ -54,6 +54,7 @@ SIGNATURES = {
     "tnmc_build_env_variational": ([ctypes.POINTER(_Lattice), ctypes.c_double, _INT, _INT, _INT, _P,
                                     ctypes.POINTER(_P)], _INT),
     "tnmc_env_free": ([_P], _INT),
+    "tnmc_env_set_order": ([_P, _INT], _INT),
     "tnmc_env_info": ([_P, ctypes.POINTER(_Info)], _INT),
     "tnmc_env_export": ([_P, _P, _P, _P, _P, _P], _INT),
     "tnmc_env_status": ([_P, ctypes.POINTER(ctypes.c_int32)], _INT),
@@ -228,6 +229,11 @@ class Env:
         s = ctypes.c_int32()
         _check(lib().tnmc_env_status(self._h, ctypes.byref(s)))
         return s.value
+
+    def set_order(self, order):
+        """Site order of later sampling calls: "raster" or "snake" (odd rows right to left)."""
+        _check(lib().tnmc_env_set_order(self._h, {"raster": 0, "snake": 1}[order]))
+        return self
 
     def free(self):
         if self._h is not None and self._h.value:

@@ -402,6 +402,18 @@ static tnmc_status check_precision(const tnmc_env* env, int precision) {
     tnmc_set_error("the env was built without the sampler copy for precision %d", precision);
     return TNMC_E_UNSUPPORTED;
   }
+  if (env->d.order == TNMC_ORDER_SNAKE && precision == TNMC_BF16) {
+    tnmc_set_error("the BF16 tensor-core sampler runs in raster order only");
+    return TNMC_E_UNSUPPORTED;
+  }
+  return TNMC_OK;
+}
+
+tnmc_status tnmc_env_set_order(tnmc_env* env, int order) {
+  g_err[0] = 0;
+  CHECK_ARG(env, "env must be non-null");
+  CHECK_ARG(order == TNMC_ORDER_RASTER || order == TNMC_ORDER_SNAKE, "unknown site order %d", order);
+  env->d.order = order;
   return TNMC_OK;
 }
 
@@ -494,6 +506,10 @@ tnmc_status tnmc_logq_backward(const tnmc_env* env, int64_t B, const int8_t* spi
   CHECK_ARG(grad && (B == 0 || (spins && weights)), "spins, weights and grad must be non-null");
   tnmc_status st = check_precision(env, TNMC_F32);
   if (st != TNMC_OK) return st;
+  if (env->d.order != TNMC_ORDER_RASTER) {
+    tnmc_set_error("tnmc_logq_backward differentiates the raster-order q only");
+    return TNMC_E_UNSUPPORTED;
+  }
   if (env->d.P > 52) {
     tnmc_set_error("tnmc_logq_backward supports padded bond dimension P <= 52 (got %d)", env->d.P);
     return TNMC_E_UNSUPPORTED;

@@ -31,6 +31,7 @@ struct DeviceEnv {
   int z2;             // 1 when every field is zero: the builder uses parity sectors
   int gauge;          // 0: spin basis; 1: bond basis (rows sampled from the untruncated 2 chi MPS)
   int sweeps;         // two-site variational rounds after successive SVD (0: successive SVD only)
+  int order;          // site order of the samplers: TNMC_ORDER_RASTER, TNMC_ORDER_SNAKE
   const double* Jh;   // device copies of the couplings
   const double* Jv;
   const double* h;
