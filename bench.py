@@ -40,6 +40,8 @@ CONFIGS = {
                                                        "16 chains each: frozen-line TNMH moves (random cuts), Delta diagnostic"),
     "c3d": ("gaussian_ea_batch", 32, 32, "f64", "256 Gaussian EA instances 32x32, T=0.212, chi=16, 32 chains each: "
                                                "TNMH move + one Metropolis sweep per iteration, Delta diagnostic"),
+    "c6": ("cubic_ferromagnet", 65536, 512, "f32", "16x16x16 ferromagnet (open boundaries), T=4.5, D=2, chi=2: 3D TNMH "
+                                                 "proposals + MH (Sec. 3D, rejection-rate figure setting)"),
 }
 
 # the paper's Table hb row for TNMH + Metropolis: iterations to reach each Delta threshold
@@ -442,6 +444,7 @@ def run_batched(args):
         torch.cuda.synchronize()
         ks.append(k0.elapsed_time(k1))
     kern_s = statistics.mean(ks) / 1e3
+    balance, makespan_ms = plan.balance()      # of the last of these launches
     total_ms, n_accepted = replicas.reduce_timing(total_ms, n_accepted, pg, dev)
 
     # end to end: chain states of every instance uploaded from pinned host memory before,
@@ -509,6 +512,9 @@ def run_batched(args):
                    "l2": "outputs %.0f MB per step (spins + log q + energy)" % ((binf["proposal_bytes"] + 20 * props) / 1e6)},
         "proposals_per_s": round(props * world / (step_ms / 1e3), 3), "acceptance": round(acc_rate, 5),
         "flagged_fraction": float((run.prop[3] != 0).double().mean().item()),
+        "load_balance": {"efficiency": round(balance, 4), "makespan_ms": round(makespan_ms, 3),
+                         "definition": "sum of the CTAs' busy time / (grid x makespan) of one persistent launch, "
+                                       "from per-CTA global-timer stamps"},
         "env_build_s": round(env_build_s, 3), "autotune_s": round(tune_s, 3),
         "device_status_nonzero": sum(1 for s in statuses if s),
         "roofline": roof, "cpu_baseline": cpu, "plain_f64": plain,
@@ -651,6 +657,190 @@ def run_frozen(args):
         "acceptance": round(float(np.mean(acc)), 5), "delta_trajectory": [round(d, 5) for d in deltas],
         "iterations_to_delta": reached, "paper_table_hbpbc": TABLE_HBPBC,
         "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def _compress_dims_flops(dl, pp, dr, kmax):
+    """Bond dims after the successive SVD of an MPS (QR sweep: min(dl p, dr); SVD sweep:
+    min(kmax, dl, p dr)) and the FLOPs of its projections and absorptions (the Jacobi
+    sweeps of the factorisations are not counted)."""
+    dl, dr = list(dl), list(dr)
+    n = len(dl)
+    fl = 0
+    for i in range(n - 1):
+        length, b = dl[i] * pp[i], dr[i]
+        k = min(length, b)
+        fl += 2 * k * b * length + 2 * k * b * pp[i + 1] * dr[i + 1]
+        dr[i], dl[i + 1] = k, k
+    for i in range(n - 1, 0, -1):
+        a, length = dl[i], pp[i] * dr[i]
+        k = min(kmax, a, length)
+        fl += 2 * a * k * length + 2 * dl[i - 1] * pp[i - 1] * a * k
+        dl[i], dr[i - 1] = k, k
+    return dl, dr, fl
+
+
+def cube_contraction_flops(dims, chi):
+    """FLOPs per 3D proposal of the sampler's contractions (bottom and top boundary
+    products, the sandwich vectors R and Lambda, the site weights) and of the QR/SVD
+    projections of its boundary compressions, from the layer PEPS dims [Lz, Ly, Lx, 4].
+    The iterative Jacobi sweeps are left out, so this is a lower bound of the work."""
+    Lz, Ly, Lx, _ = dims.shape
+    fl = 0
+    for z in range(Lz):
+        d = dims[z]
+        bot = [None] * Ly
+        bot[Ly - 1] = [1] * (Lx + 1)
+        for y in range(Ly - 2, -1, -1):
+            dl, pp, dr = [], [], []
+            for x in range(Lx):
+                du, dlx, dd, drx = (int(v) for v in d[y + 1, x])
+                bl, br = bot[y + 1][x], bot[y + 1][x + 1]
+                fl += 3 * du * dlx * dd * drx + 2 * (dlx * bl) * du * (drx * br) * dd
+                dl.append(dlx * bl)
+                pp.append(du)
+                dr.append(drx * br)
+            dl2, _, f = _compress_dims_flops(dl, pp, dr, chi)
+            fl += f
+            bot[y] = dl2 + [1]
+        tb = [1] * (Lx + 1)
+        for y in range(Ly):
+            for x in range(Lx):
+                du, dlx, dd, drx = (int(v) for v in d[y, x])
+                ta, tc, pb, qb = tb[x], tb[x + 1], bot[y][x], bot[y][x + 1]
+                if x > 0:
+                    fl += 2 * ta * du * drx * qb * tc + 2 * ta * dlx * dd * qb * du * drx + 2 * ta * dlx * pb * dd * qb
+                fl += (2 * dlx * pb * du * tc * ta + 2 * dlx * du * tc * dd * qb * pb + 2 * dlx * du * dd * drx * tc * qb
+                       + 4 * du * dlx * dd * drx + 2 * tc * drx * qb * dlx * du * dd)
+            if y + 1 < Ly:
+                dl, pp, dr = [], [], []
+                for x in range(Lx):
+                    du, dlx, dd, drx = (int(v) for v in d[y, x])
+                    fl += 2 * (tb[x] * dlx) * dd * (tb[x + 1] * drx) * du
+                    dl.append(tb[x] * dlx)
+                    pp.append(dd)
+                    dr.append(tb[x + 1] * drx)
+                dl2, _, f = _compress_dims_flops(dl, pp, dr, chi)
+                fl += f
+                tb = dl2 + [1]
+    return fl
+
+
+def run_cube(args):
+    """Three-dimensional TNMH (Sec. 3D): the 16^3 ferromagnet with layer PEPS of bond D and
+    boundary MPS of bond chi; a step is B proposals (one thread each) and the MH scan of C
+    chains over them."""
+    import torch
+    from paper_2104_13264_gb300 import binding as Bd
+    from paper_2104_13264_gb300 import instances
+
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    fac, Bdef, Cdef, pdef, desc = CONFIGS["c6"]
+    if args.cube_model == "afm":
+        inst = instances.cubic_antiferromagnet(L=args.cube_L, T=args.cube_T, D=args.cube_D, chi=args.cube_chi)
+        desc = desc.replace("ferromagnet", "antiferromagnet in a field h=3")
+    else:
+        inst = instances.cubic_ferromagnet(L=args.cube_L, T=args.cube_T, D=args.cube_D, chi=args.cube_chi)
+    desc = desc.replace("T=4.5", "T=%g" % args.cube_T).replace("D=2, chi=2", "D=%d, chi=%d" % (inst.D, inst.chi))
+    B = args.batch or Bdef
+    C = args.chains or Cdef
+    T = B // C
+    B = C * T
+    prec = args.precision or pdef
+    stream = torch.cuda.current_stream()
+    t0 = time.time()
+    env = Bd.Env3D.from_instance(inst)
+    build_s = time.time() - t0
+    assert env.status() == 0, "3D build reported a numerical problem"
+    chain = Bd.init_chains3d(env, C, seed=args.seed + 1, precision=prec)
+    nacc = torch.zeros(1, dtype=torch.int64, device=dev)
+    acc_hist = []
+
+    def step(k):
+        sp, lq, E, fl = Bd.sample3d(env, B, seed=args.seed, sample_offset=(rank << 40) + k * B, precision=prec)
+        a = Bd.mh_step3d(env, C, T, (sp, lq, E), chain, seed=args.seed + 2, step_offset=(rank << 40) + k * T,
+                         n_accepted=nacc)
+        return a
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+    nacc.zero_()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for k in range(args.steps):
+        acc_hist.append(step(args.warmup + k))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    sec = e0.elapsed_time(e1) / 1e3
+    acc = int(nacc.item())
+    acceptance = acc / (B * args.steps)
+    # end to end: the same steps with the accepted count read back every step
+    t1 = time.time()
+    for k in range(args.steps):
+        step(args.warmup + args.steps + k)
+        _ = int(nacc.item())
+    e2e_s = time.time() - t1
+    # the plain FP64 form on a bounded subset
+    plain = None
+    if not args.no_plain:
+        nb = min(B, 2048)
+        Bd.sample3d(env, 128, seed=args.seed, precision="f64")
+        torch.cuda.synchronize()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        Bd.sample3d(env, nb, seed=args.seed, sample_offset=1 << 41, precision="f64")
+        p1.record(stream)
+        torch.cuda.synchronize()
+        ps = p0.elapsed_time(p1) / 1e3
+        plain = {"proposals": nb, "proposals_per_s": round(nb / ps, 3), "precision": "f64"}
+    dims = env.export()["dims"]
+    flops = cube_contraction_flops(dims, inst.chi)
+    ach = flops * B * args.steps / sec / 1e12
+    peak = 152 * 128 * 2 * 2070e6 / 1e12 if prec == "f32" else 1.25
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        from oracle import peps3d
+        oenv = peps3d.build_env3d(inst.Jx, inst.Jy, inst.Jz, inst.h, inst.beta, inst.D, inst.chi)
+        nb = 32
+        c0 = time.time()
+        peps3d.sample3d(oenv, nb, seed=args.seed)
+        cs = time.time() - c0
+        cpu = {"value": round(nb * acceptance / cs, 4), "unit": "accepted samples/s", "cores": 1, "kind": "oracle",
+               "sample": "%d proposals of the same 16^3 workload drawn by the numpy oracle (vectorised over samples, "
+                         "one process), times the GPU chains' acceptance" % nb,
+               "proposals_per_s": round(nb / cs, 4)}
+    if rank != 0:
+        return
+    value = acc / sec * world
+    line = {
+        "metric": "accepted samples/s (3D TNMH proposals + MH, %s)" % desc, "value": round(value, 3),
+        "unit": "accepted samples/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(sec / args.steps * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": prec, "data": "synthetic (uniform couplings)",
+        "config": {"workload": "c6", "description": desc, "model": inst.name, "L": args.cube_L, "T": args.cube_T,
+                   "D": inst.D,
+                   "chi": inst.chi, "B": B, "chains": C, "proposals_per_chain": T,
+                   "multi_gpu": "replicas only: each rank runs its own chains"},
+        "acceptance": round(acceptance, 5), "env_build_s": round(build_s, 3),
+        "roofline": {"bound": "alu", "achieved": round(ach, 4), "peak": round(peak, 3), "unit": "TFLOP/s",
+                     "frac": round(ach / peak, 5), "traffic": None, "kernel": "sample3d_kernel<%s>" % prec,
+                     "flop_per_sample": flops,
+                     "peak_source": "FP32 FFMA nominal: 152 SM x 128 lanes x 2 x 2070 MHz" if prec == "f32"
+                     else "FP64 nominal 1.25 TFLOP/s",
+                     "flop_note": "contractions and QR/SVD projections counted from the layer dims; the iterative "
+                                  "Jacobi sweeps are not counted (lower bound)"},
+        "cpu_baseline": cpu, "plain_f64": plain, "clocks": clk,
+        "e2e": {"value": round(acc / e2e_s * world, 3), "unit": "accepted samples/s",
+                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 8},
+        "gpu_launches": (2 + 2) * args.steps,
     }
     print(json.dumps(line), flush=True)
 
@@ -955,6 +1145,12 @@ def main():
     ap.add_argument("--iters", type=int, default=30, help="iterations of the Delta trajectory (c3d)")
     ap.add_argument("--gauge", default="spin", choices=["spin", "bond"],
                     help="environment gauge: spin basis, or the bond basis of App. A (chi <= 32)")
+    ap.add_argument("--cube-L", type=int, default=16, help="3D lattice side (c6)")
+    ap.add_argument("--cube-T", type=float, default=4.5, help="3D temperature (c6)")
+    ap.add_argument("--cube-D", type=int, default=2, help="3D layer PEPS bond (c6)")
+    ap.add_argument("--cube-chi", type=int, default=2, help="3D boundary MPS bond (c6)")
+    ap.add_argument("--cube-model", default="ferro", choices=["ferro", "afm"],
+                    help="3D model: ferromagnet, or antiferromagnet in a field h = 3 (c6)")
     ap.add_argument("--tune-steps", type=int, default=0,
                     help="tuning steps of the FP32 tensors before the timed sampling (the 64x64 Villain case uses 50)")
     args = ap.parse_args()
@@ -966,6 +1162,8 @@ def main():
         run_equilibration(args)
     elif args.config == "c3p":
         run_frozen(args)
+    elif args.config == "c6":
+        run_cube(args)
     else:
         run_tnmc(args)
 

@@ -417,6 +417,14 @@ tnmc_status tnmc_batch_layout(const tnmc_batch* plan, int64_t* prop_row, int64_t
  * advance adds 1 to k on the device, so a captured CUDA graph of
  * sample + mh + advance replays successive steps.
  */
+/*
+ * Load balance of the plan's last persistent sampling launch (proposals or chains):
+ * every CTA records the global timer when it starts and when it finds no item left;
+ * efficiency = sum over CTAs of their busy time / (grid x makespan), in (0, 1].
+ * Synchronises the device.  makespan_ms may be NULL.
+ */
+tnmc_status tnmc_batch_balance(const tnmc_batch* plan, double* efficiency, double* makespan_ms);
+
 tnmc_status tnmc_batch_set_step(tnmc_batch* plan, uint64_t seed, uint64_t step, void* stream);
 tnmc_status tnmc_batch_advance(tnmc_batch* plan, void* stream);
 

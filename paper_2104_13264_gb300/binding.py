@@ -73,6 +73,7 @@ SIGNATURES = {
     "tnmc_batch_info": ([_P, ctypes.POINTER(_BatchInfo)], _INT),
     "tnmc_batch_layout": ([_P, _P, _P, _P, _P], _INT),
     "tnmc_batch_set_step": ([_P, _U64, _U64, _P], _INT),
+    "tnmc_batch_balance": ([_P, _P, _P], _INT),
     "tnmc_batch_advance": ([_P, _P], _INT),
     "tnmc_sample_batched": ([_P, _P, _P, _P, _P, _P], _INT),
     "tnmc_logq_batched": ([_P, _P, _P, _P, _P, _P], _INT),
@@ -492,6 +493,12 @@ class Batch:
             out = torch.empty((self.n, self.chains // 2), dtype=torch.float64, device=chain_spins.device)
         _check(lib().tnmc_link_overlap_batched(self._h, _ptr(chain_spins), _ptr(out), _stream(stream)))
         return out
+
+    def balance(self):
+        """(efficiency, makespan ms) of the last persistent sampling launch (tnmc_batch_balance)."""
+        e, m = ctypes.c_double(), ctypes.c_double()
+        _check(lib().tnmc_batch_balance(self._h, ctypes.byref(e), ctypes.byref(m)))
+        return e.value, m.value
 
     def free(self):
         if self._h is not None and self._h.value:

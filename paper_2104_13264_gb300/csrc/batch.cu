@@ -59,13 +59,23 @@ __global__ void batch_prepare_kernel(SampleArgs<T>* tab, int n, const int64_t* r
   a.flags = flags ? flags + row_off[i] : nullptr;
 }
 
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// cta_ns[2 i], cta_ns[2 i + 1]: when CTA i started and when it found no item left (global
+// timer, ns): the load balance of the launch is sum(busy) / (grid x makespan).
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT) sample_batched_kernel(const SampleArgs<T>* __restrict__ tab,
                                                             const int2* __restrict__ items, int64_t nitems,
-                                                            unsigned int* counter, T* scratch, size_t stack_elems) {
+                                                            unsigned int* counter, T* scratch, size_t stack_elems,
+                                                            uint64_t* cta_ns) {
   extern __shared__ unsigned char smem_raw[];
   __shared__ int2 item;
   T* stack = scratch + (size_t)blockIdx.x * stack_elems;
+  if (threadIdx.x == 0) cta_ns[2 * blockIdx.x] = global_ns();
   for (;;) {
     if (threadIdx.x == 0) {
       const unsigned int k = atomicAdd(counter, 1u);
@@ -78,6 +88,7 @@ __global__ void __launch_bounds__(NT) sample_batched_kernel(const SampleArgs<T>*
     const SampleArgs<T> a = tab[it.x];
     sample_simt_tile<T, NT>(a, it.y, smem_raw, stack);
   }
+  if (threadIdx.x == 0) cta_ns[2 * blockIdx.x + 1] = global_ns();
 }
 
 // One thread per chain (g = i C + c), sequential over the chain's T_i proposals.
@@ -233,6 +244,7 @@ struct tnmc_batch {
   unsigned int* d_counter = nullptr;
   uint64_t* d_params = nullptr;
   int64_t* d_last = nullptr;
+  uint64_t* d_cta_ns = nullptr;   // [grid][2] timers of the last sampling launch
 };
 
 namespace {
@@ -314,7 +326,8 @@ tnmc_status launch_batched(tnmc_batch* p, bool chains, const int8_t* spins_in, i
   unsigned int* counter = p->d_counter + (chains ? 1 : 0);
   TNMC_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned int), s));
   sample_batched_kernel<T, NT><<<p->grid, NT, p->smem, s>>>(tab, chains ? p->d_items_chain : p->d_items_prop, nitems,
-                                                            counter, static_cast<T*>(p->scratch), p->stack_elems);
+                                                            counter, static_cast<T*>(p->scratch), p->stack_elems,
+                                                            p->d_cta_ns);
   TNMC_CUDA_TRY(cudaGetLastError());
   return TNMC_OK;
 }
@@ -452,6 +465,7 @@ tnmc_status tnmc_batch_create(int n, tnmc_env* const* envs, const int64_t* B, in
   const size_t o_mh = take(n * sizeof(tnmc::MhInst)), o_cnt = take(2 * sizeof(unsigned int));
   const size_t o_metro = take(n * sizeof(tnmc::MetroInst));
   const size_t o_par = take(2 * sizeof(uint64_t)), o_last = take((size_t)p->chain_rows * 8);
+  const size_t o_ns = take((size_t)p->grid * 2 * sizeof(uint64_t));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   p->alloc = current_allocator();
   char* base = static_cast<char*>(dev_alloc(p->alloc, off, s));
@@ -479,6 +493,7 @@ tnmc_status tnmc_batch_create(int n, tnmc_env* const* envs, const int64_t* B, in
   p->d_counter = reinterpret_cast<unsigned int*>(base + o_cnt);
   p->d_params = reinterpret_cast<uint64_t*>(base + o_par);
   p->d_last = reinterpret_cast<int64_t*>(base + o_last);
+  p->d_cta_ns = reinterpret_cast<uint64_t*>(base + o_ns);
 
   // host images of the tables, uploaded once; the call returns after the upload
   std::vector<char> tp(tab_bytes), tc(tab_bytes);
@@ -539,6 +554,25 @@ tnmc_status tnmc_batch_info(const tnmc_batch* p, tnmc_batch_info_t* info) {
   info->items = p->items_prop;
   info->smem_bytes = (int64_t)p->smem;
   info->scratch_bytes = (int64_t)p->scratch_bytes;
+  return TNMC_OK;
+}
+
+tnmc_status tnmc_batch_balance(const tnmc_batch* p, double* efficiency, double* makespan_ms) {
+  CHECK_ARG(p && efficiency, "plan and efficiency must be non-null");
+  std::vector<uint64_t> t((size_t)p->grid * 2);
+  TNMC_CUDA_TRY(cudaDeviceSynchronize());
+  TNMC_CUDA_TRY(cudaMemcpy(t.data(), p->d_cta_ns, t.size() * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+  uint64_t lo = UINT64_MAX, hi = 0;
+  double busy = 0.0;
+  for (int i = 0; i < p->grid; ++i) {
+    const uint64_t a = t[2 * i], b = t[2 * i + 1];
+    lo = a < lo ? a : lo;
+    hi = b > hi ? b : hi;
+    busy += (b > a) ? (double)(b - a) : 0.0;
+  }
+  const double span = (hi > lo) ? (double)(hi - lo) : 0.0;
+  *efficiency = span > 0.0 ? busy / ((double)p->grid * span) : 0.0;
+  if (makespan_ms) *makespan_ms = span * 1e-6;
   return TNMC_OK;
 }
 

@@ -65,11 +65,11 @@ template <typename T>
 struct Tol3;
 template <>
 struct Tol3<double> {
-  static constexpr double rot = 1e-13, null = 1e-13, big = 1e150;
+  static constexpr double rot = 1e-13, null = 1e-13, big = 1e150, qr = 1e-12;
 };
 template <>
 struct Tol3<float> {
-  static constexpr float rot = 2e-6f, null = 1e-6f, big = 1e15f;
+  static constexpr float rot = 2e-6f, null = 1e-6f, big = 1e15f, qr = 1e-5f;
 };
 
 // One-sided (Hestenes) Jacobi on the m rows (length n, row-major) of J, cyclic order.
@@ -135,8 +135,8 @@ __device__ void select_rows(V<T> d, int m, int k, int* sel) {
 }
 
 // Successive SVD of an MPS of ns sites (site i at M.at(i * cap), layout [dl][p][dr]):
-// QR sweep left to right (each site's Q from Jacobi on the rows of its transpose, R = Q^T X,
-// bond min(dl p, dr)), then SVD sweep right to left keeping min(kmax, dl, p dr) values;
+// QR sweep left to right (classical Gram-Schmidt applied twice, bond min(dl p, dr)), then
+// SVD sweep right to left keeping min(kmax, dl, p dr) values;
 // site 0 is left with unit norm.  Scratch: J >= rows x len of every step, d >= rows,
 // sm >= Kraw^2, tmp >= cap.  Returns 0 or TNMC_E_NUMERIC; *logs gets the removed scale.
 template <typename T>
@@ -148,34 +148,48 @@ __device__ int mps_compress(V<T> M, int64_t cap, int ns, int* dl, const int* pp,
   for (int i = 0; i + 1 < ns; ++i) {
     const int a = dl[i], p = pp[i], b = dr[i], len = a * p;
     V<T> Mi = M.at(i * cap);
-    if (b > kMaxRows3) return TNMC_E_NUMERIC;
-    for (int r = 0; r < b; ++r)
-      for (int x = 0; x < len; ++x) J[(int64_t)r * len + x] = Mi[(int64_t)x * b + r];
-    if (!orth_rows(J, b, len, d)) err = TNMC_E_NUMERIC;
     const int k = len < b ? len : b;
-    select_rows(d, b, k, sel);
-    const T nmax = d[sel[0]];
-    if (!(nmax > 0) || !isfinite((double)nmax)) return TNMC_E_NUMERIC;
-    T sc = 0;
-    for (int j = 0; j < k; ++j) {
-      const T nj = d[sel[j]];
-      const T inv = nj > Tol3<T>::null * nmax ? T(1) / nj : T(0);
-      for (int c = 0; c < b; ++c) {
-        T acc = 0;
-        for (int x = 0; x < len; ++x) acc += J[(int64_t)sel[j] * len + x] * Mi[(int64_t)x * b + c];
-        acc *= inv;
-        sm[(int64_t)j * b + c] = acc;
-        const T aa = acc < 0 ? -acc : acc;
-        sc = aa > sc ? aa : sc;
+    // Q R = X (len x b, X[x][c] = Mi[x b + c]) by classical Gram-Schmidt applied twice: the
+    // columns of Q (rows of J) are orthonormal; a column numerically inside the span of the
+    // earlier ones adds no basis vector, and the basis is padded with zero vectors to k
+    // (the bond width min(len, b) of a thin QR), so X = Q R still holds.
+    for (int e = 0; e < k * b; ++e) sm[e] = T(0);
+    int acc = 0;
+    for (int j = 0; j < b; ++j) {
+      T nx = 0;
+      for (int x = 0; x < len; ++x) {
+        const T v = Mi[(int64_t)x * b + j];
+        tmp[x] = v;
+        nx += v * v;
       }
+      for (int pass = 0; pass < 2; ++pass)
+        for (int q = 0; q < acc; ++q) {
+          T r = 0;
+          for (int x = 0; x < len; ++x) r += J[(int64_t)q * len + x] * tmp[x];
+          for (int x = 0; x < len; ++x) tmp[x] -= r * J[(int64_t)q * len + x];
+          sm[(int64_t)q * b + j] += r;
+        }
+      T nv = 0;
+      for (int x = 0; x < len; ++x) nv += tmp[x] * tmp[x];
+      nv = sqrt(nv);
+      if (acc < k && nv > Tol3<T>::qr * sqrt(nx) && nv > 0) {
+        const T inv = T(1) / nv;
+        for (int x = 0; x < len; ++x) J[(int64_t)acc * len + x] = tmp[x] * inv;
+        sm[(int64_t)acc * b + j] = nv;
+        ++acc;
+      }
+    }
+    for (int q = acc; q < k; ++q)
+      for (int x = 0; x < len; ++x) J[(int64_t)q * len + x] = T(0);
+    T sc = 0;
+    for (int e = 0; e < k * b; ++e) {
+      const T aa = sm[e] < 0 ? -sm[e] : sm[e];
+      sc = aa > sc ? aa : sc;
     }
     if (!(sc > 0) || !isfinite((double)sc)) return TNMC_E_NUMERIC;
     lg += log((double)sc);
-    for (int j = 0; j < k; ++j) {
-      const T nj = d[sel[j]];
-      const T inv = nj > Tol3<T>::null * nmax ? T(1) / nj : T(0);
-      for (int x = 0; x < len; ++x) Mi[(int64_t)x * k + j] = J[(int64_t)sel[j] * len + x] * inv;
-    }
+    for (int q = 0; q < k; ++q)
+      for (int x = 0; x < len; ++x) Mi[(int64_t)x * k + q] = J[(int64_t)q * len + x];
     V<T> Mn = M.at((i + 1) * cap);
     const int rest = pp[i + 1] * dr[i + 1];
     const T isc = T(1) / sc;

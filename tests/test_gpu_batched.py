@@ -207,3 +207,14 @@ def test_config3_full_size_sampled(B):
     print("flagged fraction %.3g in %d instances %s" % (frac, len(bad), bad[:20]))
     assert frac < 1e-2
     assert int(run.n_accepted.sum()) > 0
+
+
+def test_batch_balance_is_a_fraction(B):
+    from paper_2104_13264_gb300 import batched
+    insts = [instances.ea_gauss(8 + 4 * (k % 3), 8 + 4 * (k % 3), 2.0, 4, seed=k) for k in range(12)]
+    envs = B.build_envs_batched(insts, precisions=("f32",))
+    run = batched.BatchRunner(envs, 256, chains=8, precision="f32", tile=64, order="cost", tune=False, seed=1)
+    run.plan.set_step(1, 0)
+    run.plan.sample(run.prop)
+    eff, span = run.plan.balance()
+    assert 0.0 < eff <= 1.0 and span > 0.0
