@@ -48,7 +48,7 @@ import math
 import numpy as np
 
 from . import philox
-from .tnmc import threshold_plus, F_BAD
+from .tnmc import threshold_plus, vertical_split, F_BAD
 
 SPIN = np.array([-1.0, 1.0])
 
@@ -84,14 +84,19 @@ class Env3D:
         self.log_scale = np.zeros(self.Lz)
 
 
-def layer_tensors(env_next, Jx, Jy, Jz, h, beta, z):
-    """D_z H_z V_z env_{z+1} as PEPS tensors [2, Du, Dl, Dd, Dr] (in-layer bonds doubled)."""
+def layer_tensors(env_next, Jx, Jy, Jz, h, beta, z, gauge="spin"):
+    """D_z H_z V_z env_{z+1} as PEPS tensors [2, Du, Dl, Dd, Dr] (in-layer bonds doubled).
+    gauge "bond": env_{z+1} carries the index rho of the vertical bonds (z, z+1), and V'_z
+    applies their lower factor B (vertical_split) instead of summing over layer z+1."""
     _, Ly, Lx = h.shape
     out = [[None] * Lx for _ in range(Ly)]
     for y in range(Ly):
         for x in range(Lx):
             if env_next is None:
                 t = np.ones((2, 1, 1, 1, 1))
+            elif gauge == "bond":
+                Bv, _ = vertical_split(Jz[z, y, x], beta)                   # B[s, rho]
+                t = np.einsum("sp,puldr->suldr", Bv, env_next[y][x])
             else:
                 W = np.exp(beta * Jz[z, y, x] * np.outer(SPIN, SPIN))        # W[s, s']
                 t = np.einsum("ts,suldr->tuldr", W, env_next[y][x])
@@ -194,6 +199,30 @@ def build_env3d(Jx, Jy, Jz, h, beta, D, chi):
         A = layer_tensors(nxt, Jx, Jy, Jz, h, beta, z)
         env.A[z], env.log_scale[z] = compress_peps(A, D)
         nxt = env.A[z]
+    return env
+
+
+def build_env3d_bond(Jx, Jy, Jz, h, beta, D, chi):
+    """Layer environments in the bond basis (App. A: vertex tensors from split bond weights;
+    in three dimensions the vertical bonds are split as W = B T like the 2D bond gauge).
+    env'_z carries the index rho of the vertical bonds (z-1, z):
+        env'_z = T_D[ T_{z-1} D_z H_z V'_z env'_{z+1} ]   (V' applies B, T the upper factor),
+    and layer z is sampled from the uncompressed PEPS M'_z = D_z H_z V'_z env'_{z+1} of its
+    own spins (in-layer bonds up to 2D); the layer above enters through the same fields
+    f(s) = W(s_up, s).  env.A[z] holds the M'_z, which run3d samples unchanged."""
+    Jx, Jy, Jz, h, Lz, Ly, Lx = check_lattice3d(Jx, Jy, Jz, h)
+    env = Env3D(Jx, Jy, Jz, h, beta, D, chi)
+    nxt = None
+    for z in range(Lz - 1, -1, -1):
+        M = layer_tensors(nxt, Jx, Jy, Jz, h, beta, z, gauge="bond")
+        env.A[z] = M
+        if z > 0:
+            X = [[None] * Lx for _ in range(Ly)]
+            for y in range(Ly):
+                for x in range(Lx):
+                    _, Tv = vertical_split(Jz[z - 1, y, x], beta)         # T[rho, s]
+                    X[y][x] = np.einsum("ps,suldr->puldr", Tv, M[y][x])
+            nxt, env.log_scale[z] = compress_peps(X, D)
     return env
 
 

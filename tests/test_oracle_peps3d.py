@@ -123,3 +123,37 @@ def test_draw_frequencies_follow_q():
     chi2 = float(((counts[keep] - exp[keep]) ** 2 / exp[keep]).sum())
     dof = int(keep.sum()) - 1
     assert chi2 < dof + 5 * math.sqrt(2 * dof), (chi2, dof)
+
+
+# ---- the bond basis (vertical bonds split W = B T) ----
+
+@pytest.mark.parametrize("shape", [(3, 2, 2), (2, 2, 3), (2, 3, 2)])
+def test_bond_basis_exact_bonds_give_pi(shape):
+    Jx, Jy, Jz, h = random3d(*shape, seed=7 + sum(shape))
+    env = peps3d.build_env3d_bond(Jx, Jy, Jz, h, 0.7, 64, 512)
+    S, pi = boltzmann3d(Jx, Jy, Jz, h, 0.7)
+    np.testing.assert_allclose(np.exp(peps3d.logq3d(env, S)[1]), pi, rtol=1e-9, atol=1e-15)
+
+
+@pytest.mark.parametrize("shape", [(5, 1, 6), (4, 1, 7)])
+def test_bond_basis_one_row_layers_reduce_to_the_2d_bond_gauge(shape):
+    """Ly = 1: each layer is a row, the layer PEPS an MPS compressed by successive SVD, and
+    the 3D bond basis is the 2D bond gauge of the planar lattice with chi = D."""
+    Jx, Jy, Jz, h = random3d(*shape, seed=11 + shape[0])
+    beta, D = 0.9, 2
+    env3 = peps3d.build_env3d_bond(Jx, Jy, Jz, h, beta, D, 2)
+    Jh, Jv, h2 = _planar(Jx, Jy, Jz, h, "y")
+    env2 = tnmc.build_env_bond(Jh, Jv, h2, beta, D)
+    sp3, lq3, _, _ = peps3d.sample3d(env3, 150, seed=4, sample_offset=9)
+    _, lq2, _, _ = tnmc.logq(env2, sp3.reshape(150, h2.shape[0], h2.shape[1]))
+    np.testing.assert_allclose(lq3, lq2, rtol=1e-10, atol=1e-10)
+
+
+def test_bond_basis_truncated_q_is_normalised_and_better_than_spin_basis():
+    Jx, Jy, Jz, h = random3d(2, 3, 2, 8)
+    S, pi = boltzmann3d(Jx, Jy, Jz, h, 1.1)
+    qb = np.exp(peps3d.logq3d(peps3d.build_env3d_bond(Jx, Jy, Jz, h, 1.1, 1, 1), S)[1])
+    qs = np.exp(peps3d.logq3d(peps3d.build_env3d(Jx, Jy, Jz, h, 1.1, 1, 1), S)[1])
+    assert qb.sum() == pytest.approx(1.0, abs=1e-12)
+    assert 0.5 * np.abs(qb - pi).sum() > 1e-3
+    print("TV to pi: bond %.4f, spin %.4f" % (0.5 * np.abs(qb - pi).sum(), 0.5 * np.abs(qs - pi).sum()))
