@@ -752,7 +752,7 @@ def run_cube(args):
     prec = args.precision or pdef
     stream = torch.cuda.current_stream()
     t0 = time.time()
-    env = Bd.Env3D.from_instance(inst)
+    env = Bd.Env3D.from_instance(inst, gauge=args.gauge)
     build_s = time.time() - t0
     assert env.status() == 0, "3D build reported a numerical problem"
     chain = Bd.init_chains3d(env, C, seed=args.seed + 1, precision=prec)
@@ -808,7 +808,8 @@ def run_cube(args):
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         from oracle import peps3d
-        oenv = peps3d.build_env3d(inst.Jx, inst.Jy, inst.Jz, inst.h, inst.beta, inst.D, inst.chi)
+        build = peps3d.build_env3d_bond if args.gauge == "bond" else peps3d.build_env3d
+        oenv = build(inst.Jx, inst.Jy, inst.Jz, inst.h, inst.beta, inst.D, inst.chi)
         nb = 32
         c0 = time.time()
         peps3d.sample3d(oenv, nb, seed=args.seed)
@@ -826,7 +827,7 @@ def run_cube(args):
         "ms_per_step": round(sec / args.steps * 1e3, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": prec, "data": "synthetic (uniform couplings)",
         "config": {"workload": "c6", "description": desc, "model": inst.name, "L": args.cube_L, "T": args.cube_T,
-                   "D": inst.D,
+                   "gauge": args.gauge, "D": inst.D,
                    "chi": inst.chi, "B": B, "chains": C, "proposals_per_chain": T,
                    "multi_gpu": "replicas only: each rank runs its own chains"},
         "acceptance": round(acceptance, 5), "env_build_s": round(build_s, 3),
@@ -1144,7 +1145,7 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--iters", type=int, default=30, help="iterations of the Delta trajectory (c3d)")
     ap.add_argument("--gauge", default="spin", choices=["spin", "bond"],
-                    help="environment gauge: spin basis, or the bond basis of App. A (chi <= 32)")
+                    help="environment gauge: spin basis, or the bond basis of App. A (2D: chi <= 32; 3D: 2 D chi <= 64)")
     ap.add_argument("--cube-L", type=int, default=16, help="3D lattice side (c6)")
     ap.add_argument("--cube-T", type=float, default=4.5, help="3D temperature (c6)")
     ap.add_argument("--cube-D", type=int, default=2, help="3D layer PEPS bond (c6)")

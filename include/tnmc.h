@@ -513,11 +513,24 @@ typedef struct tnmc3d_env tnmc3d_env;
  * (a zero column, a Jacobi SVD that does not converge) sets the env's status word.
  */
 tnmc_status tnmc3d_build_env(const tnmc_lattice3d* lat, double beta, int D, int chi, void* stream, tnmc3d_env** out);
+/*
+ * The same in the bond basis (App. A: vertex tensors from split bond weights): each
+ * vertical bond weight is split W = B T as in tnmc_build_env_bond, the layer PEPS carries
+ * the index of the vertical bonds above it,
+ *   env'_z = T_D[ T_{z-1} D_z H_z V'_z env'_{z+1} ]   (V' applies B),
+ * and layer z is sampled from its uncompressed PEPS M'_z = D_z H_z V'_z env'_{z+1}
+ * (in-layer bonds up to 2 D); the layer above enters through the same fields.  The
+ * sampler, MH and forced evaluation run on it unchanged.  Limits as tnmc3d_build_env with
+ * 2 D chi <= 64; env_export returns the sampling tensors, padded to 2 D.
+ */
+tnmc_status tnmc3d_build_env_bond(const tnmc_lattice3d* lat, double beta, int D, int chi, void* stream,
+                                  tnmc3d_env** out);
 tnmc_status tnmc3d_env_free(tnmc3d_env* env);
 /* Synchronises and reads the status word (0 = clean; else a tnmc_status). */
 tnmc_status tnmc3d_env_status(const tnmc3d_env* env, int32_t* status);
 /*
- * Host copies (synchronous; any pointer may be NULL): tensors [Lz][Ly][Lx][2][D][D][D][D]
+ * Host copies (synchronous; any pointer may be NULL) of the tensors the sampler reads:
+ * tensors [Lz][Ly][Lx][2][P][P][P][P] with P = D (tnmc3d_build_env) or 2 D (bond basis),
  * A[s][u][l][d][r] (u: bond to row y-1, l: to column x-1, d: to row y+1, r: to column
  * x+1; zero outside the dims), dims [Lz][Ly][Lx][4] = (du, dl, dd, dr), log_scale [Lz]
  * (log of the factor removed while compressing layer z).

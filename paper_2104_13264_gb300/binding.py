@@ -93,6 +93,8 @@ class _Lattice3D(ctypes.Structure):
 
 SIGNATURES.update({
     "tnmc3d_build_env": ([ctypes.POINTER(_Lattice3D), ctypes.c_double, _INT, _INT, _P, ctypes.POINTER(_P)], _INT),
+    "tnmc3d_build_env_bond": ([ctypes.POINTER(_Lattice3D), ctypes.c_double, _INT, _INT, _P, ctypes.POINTER(_P)],
+                              _INT),
     "tnmc3d_env_free": ([_P], _INT),
     "tnmc3d_env_status": ([_P, ctypes.POINTER(ctypes.c_int32)], _INT),
     "tnmc3d_env_export": ([_P, _P, _P, _P], _INT),
@@ -516,9 +518,10 @@ class Batch:
 
 class Env3D:
     """Layer environments of a cubic-lattice instance (PEPS of bond D; the sampler's boundary
-    MPS have bond chi), built by tnmc3d_build_env."""
+    MPS have bond chi), built by tnmc3d_build_env, or by tnmc3d_build_env_bond when
+    gauge="bond" (layers sampled from their uncompressed PEPS, bond up to 2D)."""
 
-    def __init__(self, Jx, Jy, Jz, h, beta, D, chi, stream=None):
+    def __init__(self, Jx, Jy, Jz, h, beta, D, chi, stream=None, gauge="spin"):
         h = np.ascontiguousarray(h, dtype=np.float64)
         Lz, Ly, Lx = h.shape
         Jx = np.ascontiguousarray(np.asarray(Jx, dtype=np.float64).reshape(Lz, Ly, max(Lx - 1, 0)))
@@ -526,18 +529,20 @@ class Env3D:
         Jz = np.ascontiguousarray(np.asarray(Jz, dtype=np.float64).reshape(max(Lz - 1, 0), Ly, Lx))
         self.Lz, self.Ly, self.Lx = Lz, Ly, Lx
         self.beta, self.D, self.chi = float(beta), int(D), int(chi)
+        self.gauge = gauge
+        self.Ds = 2 * self.D if gauge == "bond" else self.D
         lat = _Lattice3D(Lx, Ly, Lz, Jx.ctypes.data if Jx.size else None, Jy.ctypes.data if Jy.size else None,
                          Jz.ctypes.data if Jz.size else None, h.ctypes.data)
         out = ctypes.c_void_p()
         self._h = None
-        _check(lib().tnmc3d_build_env(ctypes.byref(lat), self.beta, self.D, self.chi, _stream(stream),
-                                      ctypes.byref(out)))
+        build = {"spin": lib().tnmc3d_build_env, "bond": lib().tnmc3d_build_env_bond}[gauge]
+        _check(build(ctypes.byref(lat), self.beta, self.D, self.chi, _stream(stream), ctypes.byref(out)))
         self._h = out
 
     @classmethod
-    def from_instance(cls, inst, D=None, chi=None, stream=None):
+    def from_instance(cls, inst, D=None, chi=None, stream=None, gauge="spin"):
         return cls(inst.Jx, inst.Jy, inst.Jz, inst.h, inst.beta, inst.D if D is None else D,
-                   inst.chi if chi is None else chi, stream)
+                   inst.chi if chi is None else chi, stream, gauge)
 
     @property
     def handle(self):
@@ -548,8 +553,9 @@ class Env3D:
         return self.Lz * self.Ly * self.Lx
 
     def export(self):
-        """Host copies: tensors [Lz, Ly, Lx, 2, D, D, D, D], dims [Lz, Ly, Lx, 4], log_scale [Lz]."""
-        D = self.D
+        """Host copies of the sampling tensors [Lz, Ly, Lx, 2, P, P, P, P] (P = D, or 2D in the
+        bond basis), their dims [Lz, Ly, Lx, 4], and log_scale [Lz]."""
+        D = self.Ds
         T = np.zeros((self.Lz, self.Ly, self.Lx, 2, D, D, D, D))
         dims = np.zeros((self.Lz, self.Ly, self.Lx, 4), dtype=np.int32)
         ls = np.zeros(self.Lz)

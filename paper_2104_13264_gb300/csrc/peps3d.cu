@@ -39,6 +39,11 @@ struct tnmc3d_env {
   double* A64;  // [Lz][Ly][Lx][2][D][D][D][D]
   float* A32;
   int32_t* dims;   // [Lz][Ly][Lx][4]: du, dl, dd, dr
+  int gauge = 0;   // 1: bond basis (layers sampled from their uncompressed PEPS)
+  int Ds = 0;      // pad of the sampling tensors: D (spin basis) or 2 D (bond basis)
+  double* S64;     // sampling tensors [Lz][Ly][Lx][2][Ds]^4 (the A64 arena in the spin basis)
+  float* S32;
+  int32_t* sdims;
   double* log_scale;
   int32_t* status;
   void* arena = nullptr;
@@ -257,8 +262,24 @@ __device__ int mps_compress(V<T> M, int64_t cap, int ns, int* dl, const int* pp,
 // ---------------------------------------------------------------------------
 // Builder (FP64)
 // ---------------------------------------------------------------------------
+// The split W = B T of a vertical bond weight W[s][s'] = exp(beta J s s') (App. A), index
+// 0 <-> s = -1: eigenvectors u_0 = (1, 1)/sqrt 2, u_1 = (1, -1)/sqrt 2, eigenvalues
+// 2 cosh(beta J), 2 sinh(beta J); B[s][rho] = u_rho(s) sqrt|lambda_rho|,
+// T[rho][s] = sign(lambda_rho) sqrt|lambda_rho| u_rho(s).
+__device__ inline double bsplit3(double bj, int s, int rho) {
+  const double lam = rho ? 2.0 * sinh(bj) : 2.0 * cosh(bj);
+  const double u = (rho && s) ? -0.70710678118654752440 : 0.70710678118654752440;
+  return u * sqrt(fabs(lam));
+}
+__device__ inline double tsplit3(double bj, int rho, int s) {
+  const double lam = rho ? 2.0 * sinh(bj) : 2.0 * cosh(bj);
+  const double u = (rho && s) ? -0.70710678118654752440 : 0.70710678118654752440;
+  return (lam < 0.0 ? -1.0 : 1.0) * sqrt(fabs(lam)) * u;
+}
+
 struct Build3 {
   int Lx, Ly, Lz, D, RP;   // RP = 2 D: pad of the uncompressed layer
+  int gauge;               // 1: env_{z+1} carries the vertical bond index; V' applies B
   double beta;
   const double* Jx;
   const double* Jy;
@@ -331,7 +352,10 @@ __global__ void layer_raw_kernel(Build3 a, int z) {
         } else {
           const double bj = a.beta * a.Jz[((int64_t)z * Ly + y) * Lx + x];
           const double* An = a.A + (((int64_t)(z + 1) * Ly + y) * Lx + x) * 2 * D * D * D * D;
-          base = exp(bj * sv * -1.0) * An[pad_index(D, 0, u, l, d, r)] + exp(bj * sv) * An[pad_index(D, 1, u, l, d, r)];
+          if (a.gauge == 1)
+            base = bsplit3(bj, s, 0) * An[pad_index(D, 0, u, l, d, r)] + bsplit3(bj, s, 1) * An[pad_index(D, 1, u, l, d, r)];
+          else
+            base = exp(bj * sv * -1.0) * An[pad_index(D, 0, u, l, d, r)] + exp(bj * sv) * An[pad_index(D, 1, u, l, d, r)];
         }
         val = base * exp(a.beta * a.h[((int64_t)z * Ly + y) * Lx + x] * sv);
         if (ku == 2) val *= exp(a.beta * a.Jy[((int64_t)z * (Ly - 1) + y - 1) * Lx + x] * spin_of(cu) * sv);
@@ -452,6 +476,34 @@ __global__ void compress_rows_kernel(Build3 a, int z) {
     od[1] = dlh;
     od[2] = dd;
     od[3] = drh;
+  }
+}
+
+// Bond basis: the uncompressed layer is layer z's sampling PEPS (pad RP, its dims).
+__global__ void keep_sampling_kernel(Build3 a, int z, double* S, int32_t* sdims) {
+  const int64_t n = (int64_t)a.Ly * a.Lx * 2 * a.RP * a.RP * a.RP * a.RP;
+  double* dst = S + (int64_t)z * n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = a.raw[i];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)a.Ly * a.Lx * 4;
+       i += (int64_t)gridDim.x * blockDim.x)
+    sdims[(int64_t)z * a.Ly * a.Lx * 4 + i] = a.rdims[i];
+}
+
+// Bond basis: the upper factor T of the vertical bonds (z-1, z) on the physical leg of the
+// uncompressed layer, before it is compressed: X[rho] = sum_s T[rho][s] M[s].
+__global__ void apply_upper_factor_kernel(Build3 a, int z) {
+  const int RP = a.RP;
+  const int64_t half = (int64_t)RP * RP * RP * RP;
+  const int64_t total = (int64_t)a.Ly * a.Lx * half;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t site = i / half, e = i % half;
+    const int y = (int)(site / a.Lx), x = (int)(site % a.Lx);
+    const double bj = a.beta * a.Jz[((int64_t)(z - 1) * a.Ly + y) * a.Lx + x];
+    double* t = a.raw + site * 2 * half;
+    const double v0 = t[e], v1 = t[half + e];
+    t[e] = tsplit3(bj, 0, 0) * v0 + tsplit3(bj, 0, 1) * v1;
+    t[half + e] = tsplit3(bj, 1, 0) * v0 + tsplit3(bj, 1, 1) * v1;
   }
 }
 
@@ -799,7 +851,8 @@ static size_t align256_3(size_t b) { return (b + 255) & ~(size_t)255; }
 
 extern "C" {
 
-tnmc_status tnmc3d_build_env(const tnmc_lattice3d* lat, double beta, int D, int chi, void* stream, tnmc3d_env** out) {
+static tnmc_status build3d(const tnmc_lattice3d* lat, double beta, int D, int chi, int gauge, void* stream,
+                           tnmc3d_env** out) {
   using namespace tnmc;
   CHECK3(lat && out, "lat and out must be non-null");
   *out = nullptr;
@@ -807,8 +860,9 @@ tnmc_status tnmc3d_build_env(const tnmc_lattice3d* lat, double beta, int D, int 
   CHECK3(Lx >= 1 && Ly >= 1 && Lz >= 1 && Lx <= kMaxSide3 && Ly <= kMaxSide3 && Lz <= 4096,
          "lattice %d x %d x %d out of range (in-layer sides <= %d)", Lz, Ly, Lx, kMaxSide3);
   CHECK3(D >= 1 && D <= 8, "D = %d must be in [1, 8]", D);
-  CHECK3(chi >= 1 && chi <= 32 && D * chi <= kMaxRows3, "chi = %d must be in [1, 32] with D chi <= %d", chi,
-         kMaxRows3);
+  const int Ds = gauge ? 2 * D : D;
+  CHECK3(chi >= 1 && chi <= 32 && Ds * chi <= kMaxRows3, "chi = %d must be in [1, 32] with %sD chi <= %d", chi,
+         gauge ? "2 " : "", kMaxRows3);
   CHECK3(isfinite(beta) && beta >= 0.0, "beta must be finite and >= 0");
   CHECK3(lat->h && (Lx == 1 || lat->Jx) && (Ly == 1 || lat->Jy) && (Lz == 1 || lat->Jz), "couplings must be non-null");
   const size_t nJx = (size_t)Lz * Ly * (Lx - 1), nJy = (size_t)Lz * (Ly - 1) * Lx, nJz = (size_t)(Lz - 1) * Ly * Lx;
@@ -828,6 +882,9 @@ tnmc_status tnmc3d_build_env(const tnmc_lattice3d* lat, double beta, int D, int 
   const size_t oJx = take((nJx ? nJx : 1) * 8), oJy = take((nJy ? nJy : 1) * 8), oJz = take((nJz ? nJz : 1) * 8);
   const size_t oh = take(nh * 8), oA64 = take(nh * site * 8), oA32 = take(nh * site * 4);
   const size_t odims = take(nh * 4 * 4), ols = take((size_t)Lz * 8), ost = take(8);
+  const size_t ssite = 2 * (size_t)Ds * Ds * Ds * Ds;
+  const size_t oS64 = gauge ? take(nh * ssite * 8) : 0, oS32 = gauge ? take(nh * ssite * 4) : 0;
+  const size_t osd = gauge ? take(nh * 4 * 4) : 0;
   tnmc3d_env* env = new (std::nothrow) tnmc3d_env();
   if (!env) {
     tnmc_set_error("host allocation failed");
@@ -857,6 +914,11 @@ tnmc_status tnmc3d_build_env(const tnmc_lattice3d* lat, double beta, int D, int 
   env->dims = reinterpret_cast<int32_t*>(base + odims);
   env->log_scale = reinterpret_cast<double*>(base + ols);
   env->status = reinterpret_cast<int32_t*>(base + ost);
+  env->gauge = gauge;
+  env->Ds = Ds;
+  env->S64 = gauge ? reinterpret_cast<double*>(base + oS64) : env->A64;
+  env->S32 = gauge ? reinterpret_cast<float*>(base + oS32) : env->A32;
+  env->sdims = gauge ? reinterpret_cast<int32_t*>(base + osd) : env->dims;
   // builder scratch
   const int RP = 2 * D;
   const int L = Lx > Ly ? Lx : Ly;
@@ -884,6 +946,7 @@ tnmc_status tnmc3d_build_env(const tnmc_lattice3d* lat, double beta, int D, int 
     a.Lz = Lz;
     a.D = D;
     a.RP = RP;
+    a.gauge = gauge;
     a.beta = beta;
     a.Jx = env->Jx;
     a.Jy = env->Jy;
@@ -900,13 +963,20 @@ tnmc_status tnmc3d_build_env(const tnmc_lattice3d* lat, double beta, int D, int 
     a.status = env->status;
     for (int z = Lz - 1; z >= 0 && st == TNMC_OK; --z) {
       layer_raw_kernel<<<1024, 256, 0, s>>>(a, z);
+      if (gauge) {
+        keep_sampling_kernel<<<1024, 256, 0, s>>>(a, z, env->S64, env->sdims);
+        if (z == 0) break;            // env'_0 is never used
+        apply_upper_factor_kernel<<<1024, 256, 0, s>>>(a, z);
+      }
       compress_cols_kernel<<<1, Lx, 0, s>>>(a);
       compress_rows_kernel<<<1, Ly, 0, s>>>(a, z);
       layer_logscale_kernel<<<1, 32, 0, s>>>(a, z);
       if (cudaGetLastError() != cudaSuccess) st = TNMC_E_CUDA;
     }
+    if (st == TNMC_OK && cudaGetLastError() != cudaSuccess) st = TNMC_E_CUDA;
     if (st != TNMC_OK) break;
     to_f32_kernel<<<1024, 256, 0, s>>>(env->A64, env->A32, (int64_t)(nh * site));
+    if (gauge) to_f32_kernel<<<1024, 256, 0, s>>>(env->S64, env->S32, (int64_t)(nh * ssite));
     if (cudaGetLastError() != cudaSuccess) { st = TNMC_E_CUDA; break; }
     if (cudaStreamSynchronize(s) != cudaSuccess) { st = TNMC_E_CUDA; break; }
   } while (0);
@@ -920,6 +990,15 @@ tnmc_status tnmc3d_build_env(const tnmc_lattice3d* lat, double beta, int D, int 
   }
   *out = env;
   return TNMC_OK;
+}
+
+tnmc_status tnmc3d_build_env(const tnmc_lattice3d* lat, double beta, int D, int chi, void* stream, tnmc3d_env** out) {
+  return build3d(lat, beta, D, chi, 0, stream, out);
+}
+
+tnmc_status tnmc3d_build_env_bond(const tnmc_lattice3d* lat, double beta, int D, int chi, void* stream,
+                                  tnmc3d_env** out) {
+  return build3d(lat, beta, D, chi, 1, stream, out);
 }
 
 tnmc_status tnmc3d_env_free(tnmc3d_env* env) {
@@ -942,9 +1021,9 @@ tnmc_status tnmc3d_env_export(const tnmc3d_env* env, double* tensors, int32_t* d
   CHECK3(env, "env must be non-null");
   TNMC_CUDA_TRY(cudaDeviceSynchronize());
   const size_t nh = (size_t)env->Lz * env->Ly * env->Lx;
-  const size_t site = 2 * (size_t)env->D * env->D * env->D * env->D;
-  if (tensors) TNMC_CUDA_TRY(cudaMemcpy(tensors, env->A64, nh * site * 8, cudaMemcpyDeviceToHost));
-  if (dims) TNMC_CUDA_TRY(cudaMemcpy(dims, env->dims, nh * 16, cudaMemcpyDeviceToHost));
+  const size_t site = 2 * (size_t)env->Ds * env->Ds * env->Ds * env->Ds;
+  if (tensors) TNMC_CUDA_TRY(cudaMemcpy(tensors, env->S64, nh * site * 8, cudaMemcpyDeviceToHost));
+  if (dims) TNMC_CUDA_TRY(cudaMemcpy(dims, env->sdims, nh * 16, cudaMemcpyDeviceToHost));
   if (log_scale) TNMC_CUDA_TRY(cudaMemcpy(log_scale, env->log_scale, (size_t)env->Lz * 8, cudaMemcpyDeviceToHost));
   return TNMC_OK;
 }
@@ -957,7 +1036,7 @@ static tnmc_status run3d(const tnmc3d_env* env, int precision, int64_t B, uint64
   CHECK3(B >= 0, "B must be >= 0");
   if (B == 0) return TNMC_OK;
   CHECK3(spins && logq && energy, "spins, logq and energy must be non-null");
-  const Lay3 o = lay3(env->Lx, env->Ly, env->D, env->chi);
+  const Lay3 o = lay3(env->Lx, env->Ly, env->Ds, env->chi);
   const size_t esz = precision == TNMC_F64 ? 8 : 4;
   const size_t per = o.total * esz + (size_t)env->Ly * (env->Lx + 1) * 4;
   const size_t budget = (size_t)4 << 30;
@@ -975,15 +1054,15 @@ static tnmc_status run3d(const tnmc3d_env* env, int precision, int64_t B, uint64
   a.Lx = env->Lx;
   a.Ly = env->Ly;
   a.Lz = env->Lz;
-  a.D = env->D;
+  a.D = env->Ds;
   a.chi = env->chi;
   a.beta = env->beta;
   a.Jx = env->Jx;
   a.Jy = env->Jy;
   a.Jz = env->Jz;
   a.h = env->h;
-  a.A = precision == TNMC_F64 ? static_cast<const void*>(env->A64) : static_cast<const void*>(env->A32);
-  a.dims = env->dims;
+  a.A = precision == TNMC_F64 ? static_cast<const void*>(env->S64) : static_cast<const void*>(env->S32);
+  a.dims = env->sdims;
   a.status = env->status;
   a.seed = seed;
   a.offset = offset;

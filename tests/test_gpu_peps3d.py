@@ -121,3 +121,76 @@ def test_truncated_instance_acceptance_is_below_one(B):
     chain = B.init_chains3d(env, C, seed=3)
     acc = B.mh_step3d(env, C, T, prop, chain, seed=4).view(C, T)[:, 8:].float().mean().item()
     assert 0.0 < acc < 0.999
+
+
+# ---- the bond basis (tnmc3d_build_env_bond) ----
+
+BOND_CASES = [instances.cubic_random(3, 4, 5, 0.6, 2, 3, seed=1), instances.cubic_random(2, 5, 3, 0.8, 2, 4, seed=2),
+              instances.cubic_random(4, 3, 3, 0.5, 1, 2, seed=3, hscale=0.5), instances.cubic_random(3, 3, 4, 0.4, 4, 8, seed=6)]
+
+
+@pytest.mark.parametrize("idx", range(len(BOND_CASES)))
+def test_bond_basis_matches_oracle(B, idx):
+    inst = BOND_CASES[idx]
+    ref = peps3d.build_env3d_bond(inst.Jx, inst.Jy, inst.Jz, inst.h, inst.beta, inst.D, inst.chi)
+    env = B.Env3D.from_instance(inst, gauge="bond")
+    assert env.status() == 0
+    ex = env.export()
+    for z in range(inst.shape[0]):
+        for y in range(inst.shape[1]):
+            for x in range(inst.shape[2]):
+                assert tuple(ex["dims"][z, y, x]) == ref.A[z][y][x].shape[1:], (z, y, x)
+    n = 301
+    sp, lq, E, fl = B.sample3d(env, n, seed=7, sample_offset=5)
+    torch.cuda.synchronize()
+    osp, olq, _, ofl = peps3d.sample3d(ref, n, seed=7, sample_offset=5)
+    sp_h = sp.cpu().numpy()
+    assert np.all(fl.cpu().numpy() == 0) and np.all(ofl == 0)
+    same = np.all(sp_h.reshape(n, -1) == osp.reshape(n, -1), axis=1)
+    assert same.mean() >= 0.98, same.mean()
+    np.testing.assert_allclose(lq.cpu().numpy()[same], olq[same], rtol=1e-9, atol=1e-9)
+    if not same.all():
+        np.testing.assert_allclose(lq.cpu().numpy()[~same], peps3d.logq3d(ref, sp_h[~same])[1], rtol=1e-9, atol=1e-9)
+    sp2, lq2, _, _ = B.sample3d(env, 200, seed=9, precision="f32")
+    torch.cuda.synchronize()
+    olq2 = peps3d.logq3d(ref, sp2.cpu().numpy())[1]
+    err = np.abs(lq2.cpu().numpy() - olq2) / np.abs(olq2)
+    print("3D bond basis FP32 log q: max relative error %.2e" % err.max())
+    assert err.max() < 1e-5
+
+
+def test_bond_basis_exact_bonds_accept_everything(B):
+    inst = instances.cubic_random(2, 3, 2, 0.6, 8, 4, seed=4)
+    env = B.Env3D.from_instance(inst, gauge="bond")
+    C, T = 64, 16
+    prop = B.sample3d(env, C * T, seed=2)[:3]
+    chain = B.init_chains3d(env, C, seed=3)
+    acc = B.mh_step3d(env, C, T, prop, chain, seed=4)
+    assert acc.float().mean().item() > 0.999
+
+
+@pytest.mark.parametrize("gauge", ["spin", "bond"])
+def test_3d_chain_energy_matches_enumeration(B, gauge):
+    """MH with truncated 3D proposals is exact: the chains' mean energy agrees with the
+    Boltzmann average (enumeration of the 2^18 states) within 3 sigma (batch means)."""
+    inst = instances.cubic_random(2, 3, 3, 0.7, 1, 1, seed=12, hscale=0.4)
+    S = (2 * ((np.arange(2 ** 18)[:, None] >> np.arange(18)[None]) & 1) - 1).reshape(-1, 2, 3, 3).astype(np.int8)
+    Eall = peps3d.energy3d(inst.Jx, inst.Jy, inst.Jz, inst.h, S)
+    a = -inst.beta * Eall
+    w = np.exp(a - a.max())
+    exact_E = float((w * Eall).sum() / w.sum())
+    env = B.Env3D.from_instance(inst, gauge=gauge)
+    C, T, steps, burn = 256, 4, 40, 10
+    chain = B.init_chains3d(env, C, seed=5)
+    means, acc = [], []
+    for k in range(steps):
+        prop = B.sample3d(env, C * T, seed=9, sample_offset=k * C * T)[:3]
+        acc.append(B.mh_step3d(env, C, T, prop, chain, seed=10, step_offset=k * T).float().mean().item())
+        if k >= burn:
+            means.append(chain[2].cpu().numpy())
+    per_chain = np.mean(np.array(means), axis=0)          # time average of each chain
+    est = float(per_chain.mean())
+    err = float(per_chain.std(ddof=1) / np.sqrt(C))
+    print("3D %s chains: <E> %.4f +- %.4f, exact %.4f, acceptance %.3f" % (gauge, est, err, exact_E, np.mean(acc)))
+    assert 0.0 < np.mean(acc) < 1.0
+    assert abs(est - exact_E) < 3 * err + 1e-9
