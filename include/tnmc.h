@@ -335,7 +335,7 @@ tnmc_status tnmc_link_overlap(const tnmc_env* env, int64_t C, const int8_t* chai
  * spins    device int8 [B][Ly][Lx]
  * weights  device float [B]; samples whose log q is -inf must have weight 0
  * grad     device float, same layout as the parameters ([Ly][Lx][P][2][P]);
- *          overwritten.  Requires the TNMC_F32 copy and P <= 52.
+ *          overwritten.  Requires the TNMC_F32 copy and P <= 64 (64 samples per CTA above P = 52).
  */
 tnmc_status tnmc_logq_backward(const tnmc_env* env, int64_t B, const int8_t* spins, const float* weights,
                                float* grad, void* stream);

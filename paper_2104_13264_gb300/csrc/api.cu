@@ -510,8 +510,8 @@ tnmc_status tnmc_logq_backward(const tnmc_env* env, int64_t B, const int8_t* spi
     tnmc_set_error("tnmc_logq_backward differentiates the raster-order q only");
     return TNMC_E_UNSUPPORTED;
   }
-  if (env->d.P > 52) {
-    tnmc_set_error("tnmc_logq_backward supports padded bond dimension P <= 52 (got %d)", env->d.P);
+  if (env->d.P > 64) {
+    tnmc_set_error("tnmc_logq_backward supports padded bond dimension P <= 64 (got %d)", env->d.P);
     return TNMC_E_UNSUPPORTED;
   }
   return tnmc_launch_logq_grad(env, B, spins, weights, grad, static_cast<cudaStream_t>(stream));

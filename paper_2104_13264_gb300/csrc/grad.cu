@@ -24,8 +24,8 @@
 namespace tnmc {
 namespace {
 
-constexpr int kNT = 128;
-constexpr int kSP = kNT + 1;   // shared-memory stride per vector component (conflict free)
+// NT samples per CTA (one per thread); vectors live in shared memory with stride NT + 1
+// (conflict free).  128 up to P = 52; 64 above, so that P = 64 fits the shared memory.
 
 struct GradArgs {
   DeviceEnv e;
@@ -41,7 +41,9 @@ struct GradArgs {
 
 __device__ inline float scale2f(float x, int e) { return scalbnf(x, e); }
 
+template <int kNT>
 __global__ void __launch_bounds__(kNT) logq_grad_kernel(GradArgs a) {
+  constexpr int kSP = kNT + 1;
   extern __shared__ float sm[];
   const int Lx = a.e.Lx, Ly = a.e.Ly, P = a.e.P;
   const int W = (Lx + 31) >> 5;
@@ -249,15 +251,22 @@ tnmc_status tnmc_launch_logq_grad(const tnmc_env* env, int64_t B, const int8_t* 
   TNMC_CUDA_TRY(cudaMemsetAsync(grad, 0, gsz * sizeof(float), stream));
   if (B == 0) return TNMC_OK;
   const int W = (d.Lx + 31) / 32;
-  const size_t smem = (size_t)7 * d.P * kSP * sizeof(float) + (size_t)2 * W * kNT * sizeof(uint32_t);
   int dev = 0, max_optin = 0;
   TNMC_CUDA_TRY(cudaGetDevice(&dev));
   TNMC_CUDA_TRY(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  auto smem_of = [&](int nt) {
+    return (size_t)7 * d.P * (nt + 1) * sizeof(float) + (size_t)2 * W * nt * sizeof(uint32_t);
+  };
+  const int kNT = smem_of(128) <= (size_t)max_optin ? 128 : 64;
+  const size_t smem = smem_of(kNT);
   if (smem > (size_t)max_optin) {
     tnmc_set_error("gradient kernel needs %zu bytes of shared memory (device allows %d)", smem, max_optin);
     return TNMC_E_UNSUPPORTED;
   }
-  TNMC_CUDA_TRY(cudaFuncSetAttribute(logq_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (kNT == 128)
+    TNMC_CUDA_TRY(cudaFuncSetAttribute(logq_grad_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  else
+    TNMC_CUDA_TRY(cudaFuncSetAttribute(logq_grad_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int64_t ntiles = (B + kNT - 1) / kNT;
   const size_t per_cta = (size_t)3 * (d.Lx + 1) * d.P * kNT + (size_t)4 * d.Lx * kNT;
   const size_t need = (size_t)ntiles * per_cta * sizeof(float);
@@ -276,7 +285,8 @@ tnmc_status tnmc_launch_logq_grad(const tnmc_env* env, int64_t B, const int8_t* 
   a.weights = weights;
   a.grad = grad;
   a.scratch = static_cast<float*>(me->scratch.ptr);
-  logq_grad_kernel<<<(unsigned)ntiles, kNT, smem, stream>>>(a);
+  if (kNT == 128) logq_grad_kernel<128><<<(unsigned)ntiles, 128, smem, stream>>>(a);
+  else logq_grad_kernel<64><<<(unsigned)ntiles, 64, smem, stream>>>(a);
   TNMC_CUDA_TRY(cudaGetLastError());
   return TNMC_OK;
 }

@@ -46,7 +46,9 @@ def _flat(env_g, ts, inst):
 
 
 CASES = [instances.villain(4, 5, 1.5, 2), instances.random_small(5, 6, 0.8, 4, seed=2),
-         instances.ea_pm(6, 7, 1.0, 8, seed=3), instances.random_small(3, 19, 0.7, 8, seed=4)]
+         instances.ea_pm(6, 7, 1.0, 8, seed=3), instances.random_small(3, 19, 0.7, 8, seed=4),
+         # chi = 64 with bonds that reach 64 (P = 64: the 64-sample tile of the backward)
+         instances.random_small(8, 14, 0.6, 64, seed=5)]
 
 
 @pytest.mark.parametrize("idx", range(len(CASES)))
