@@ -585,7 +585,7 @@ __device__ __forceinline__ T absT(T v) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(128) sample3d_kernel(Samp3 a) {
+__global__ void __launch_bounds__(128, 4) sample3d_kernel(Samp3 a) {
   const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (b >= a.Bc) return;
   const int64_t g = a.b0 + b;
