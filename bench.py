@@ -378,6 +378,68 @@ def run_tnmc(args):
         pg.destroy_process_group()
 
 
+def run_batched_mixed(args):
+    """Config 3 with the sampler chosen per chi class (batched.MixedRunner): chi < tc_chi on
+    the persistent FP32 plan, chi >= tc_chi on the BF16 tensor-core sampler, one stream per
+    instance, all concurrent.  Timed region: K steps, CUDA events on the current stream."""
+    import torch
+    from paper_2104_13264_gb300 import batched, instances
+
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    fac, Bdef, Cdef, pdef, desc = CONFIGS["c3"]
+    insts = instances.config3()
+    B = args.batch or Bdef
+    C = args.chains or Cdef
+    t0 = time.time()
+    run = batched.MixedRunner(insts, B, C, tc_chi=args.tc_chi, seed=args.seed + 7919 * rank)
+    build_s = time.time() - t0
+    for _ in range(args.warmup):
+        run.step()
+    torch.cuda.synchronize()
+    run.reset_counts()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        run.step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    sec = e0.elapsed_time(e1) / 1e3
+    acc = run.n_accepted()
+    props = B * len(insts) * args.steps
+    flops = sum(algorithmic_flops(i) for i in insts) * B * args.steps
+    ach = flops / sec / 1e12
+    peaks, peak_src = load_peaks()
+    peak = peaks["bf16_tflops_sustained"]
+    if rank != 0:
+        return
+    line = {
+        "metric": "accepted samples/s (TNMH proposals + MH, %s)" % desc, "value": round(acc / sec * world, 3),
+        "unit": "accepted samples/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(sec / args.steps * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 (chi < %d) + bf16 (chi >= %d)" % (args.tc_chi, args.tc_chi),
+        "data": "synthetic (seeded Gaussian couplings)",
+        "config": {"workload": "c3", "description": desc, "instances": len(insts), "B": B, "chains": C,
+                   "tc_chi": args.tc_chi, "tensor_core_instances": len(run.big_idx),
+                   "fp32_instances": len(run.small_idx), "form": "per-chi-class samplers on concurrent streams"},
+        "acceptance": round(acc / props, 5), "proposals_per_s": round(props / sec * world, 3),
+        "flagged_fraction": run.flagged_fraction(), "env_build_s": round(build_s, 3),
+        "roofline": {"bound": "tensor", "achieved": round(ach, 3), "peak": peak, "unit": "TFLOP/s",
+                     "frac": round(ach / peak, 5), "traffic": None, "kernel": "whole step",
+                     "peak_source": "bf16_tflops_sustained (%s)" % peak_src,
+                     "note": "algorithmic FLOPs of every instance over the whole step time, against the sustained "
+                             "BF16 peak (most of the work is on the tensor cores)"},
+        "cpu_baseline": None, "e2e": None, "clocks": clk,
+        "gpu_launches": (2 * len(run.big_idx) + 4) * args.steps,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_batched(args):
     """The batched persistent form: every instance's proposals in one persistent launch,
     the MH scan of every chain in one launch, both replayed from a captured CUDA graph;
@@ -1146,6 +1208,8 @@ def main():
     ap.add_argument("--iters", type=int, default=30, help="iterations of the Delta trajectory (c3d)")
     ap.add_argument("--gauge", default=None, choices=["spin", "bond"],
                     help="environment gauge: spin basis, or the bond basis of App. A (2D: chi <= 32; 3D: 2 D chi <= 64)")
+    ap.add_argument("--tc-chi", type=int, default=0,
+                    help="config 3: instances with chi >= this use the BF16 tensor-core sampler (0: all FP32 batched)")
     ap.add_argument("--cube-L", type=int, default=16, help="3D lattice side (c6)")
     ap.add_argument("--cube-T", type=float, default=4.5, help="3D temperature (c6)")
     ap.add_argument("--cube-D", type=int, default=2, help="3D layer PEPS bond (c6)")
@@ -1160,6 +1224,8 @@ def main():
         args.gauge = "bond" if args.config == "c6" else "spin"
     if args.impl == "reference":
         run_reference(args)
+    elif args.config == "c3" and args.tc_chi:
+        run_batched_mixed(args)
     elif args.config == "c3":
         run_batched(args)
     elif args.config == "c3d":

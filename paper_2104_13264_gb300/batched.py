@@ -155,3 +155,82 @@ class BatchRunner:
         if self.graph is None:
             self.capture()
         self.graph.replay()
+
+
+class MixedRunner:
+    """MH steps over many instances with the sampler chosen per chi class: instances with
+    chi < tc_chi share one persistent FP32 plan (BatchRunner, graph replay); each instance
+    with chi >= tc_chi draws its proposals with the BF16 tensor-core sampler (tnmc_sample)
+    and runs its own MH scan (tnmc_mh_step), on a stream of its own, concurrently with the
+    plan.  The small instances are the plan's instances 0 .. n_small - 1 with the plan's
+    counters; the j-th large one has instance index n_small + j, so at step k it draws
+    sample indices ((n_small + j) << 40) + k B and MH step offsets ((n_small + j) << 40) + k T
+    (chain c of the instance is MH chain c): every instance has its own random streams."""
+
+    def __init__(self, insts, B, chains, tc_chi=32, seed=0, tune=True, log=None):
+        import torch
+        self.B, self.C, self.T = int(B), int(chains), int(B) // int(chains)
+        self.seed = int(seed)
+        self.small_idx = [i for i, x in enumerate(insts) if x.chi < tc_chi]
+        self.big_idx = [i for i, x in enumerate(insts) if x.chi >= tc_chi]
+        self.small_envs = binding.build_envs_batched([insts[i] for i in self.small_idx], precisions=("f32",)) \
+            if self.small_idx else []
+        self.big_envs = binding.build_envs_batched([insts[i] for i in self.big_idx], precisions=("bf16",)) \
+            if self.big_idx else []
+        self.small = BatchRunner(self.small_envs, B, chains=chains, precision="f32", seed=seed, tune=tune,
+                                 log=log) if self.small_envs else None
+        dev = torch.device("cuda")
+        # the tensor-core instances go first and on high-priority streams, largest first, so
+        # that their long tiles start before the persistent plan fills the SMs
+        try:
+            hi = torch.cuda.Stream.priority_range()[1]
+        except (AttributeError, RuntimeError):
+            hi = 0
+        self.streams = [torch.cuda.Stream(priority=hi) for _ in self.big_envs]
+        self.order = sorted(range(len(self.big_envs)), key=lambda j: -self.big_envs[j].Lx * self.big_envs[j].Ly)
+        self.big_prop, self.big_chain = [], []
+        for e in self.big_envs:
+            self.big_prop.append((torch.empty((self.B, e.Ly, e.Lx), dtype=torch.int8, device=dev),
+                                  torch.empty(self.B, dtype=torch.float64, device=dev),
+                                  torch.empty(self.B, dtype=torch.float64, device=dev),
+                                  torch.empty(self.B, dtype=torch.int32, device=dev)))
+            self.big_chain.append(binding.init_chains(e, self.C, seed=seed + 1, precision="bf16"))
+        self.big_accepted = torch.zeros(len(self.big_envs), dtype=torch.int64, device=dev)
+        self.k = 0
+
+    def step(self):
+        import torch
+        cur = torch.cuda.current_stream()
+        k = self.k
+        for j in self.order:
+            e, s = self.big_envs[j], self.streams[j]
+            s.wait_stream(cur)
+            i = len(self.small_idx) + j
+            sp, lq, E, fl = self.big_prop[j]
+            binding.sample(e, self.B, seed=self.seed, sample_offset=(i << 40) + k * self.B, precision="bf16",
+                           out=(sp, lq, E, fl), stream=s)
+            binding.mh_step(e, self.C, self.T, (sp, lq, E), self.big_chain[j], seed=self.seed,
+                            step_offset=(i << 40) + k * self.T, n_accepted=self.big_accepted[j:j + 1], stream=s)
+        if self.small is not None:
+            self.small.step()
+        for s in self.streams:
+            cur.wait_stream(s)
+        self.k += 1
+
+    def n_accepted(self):
+        tot = int(self.big_accepted.sum().item())
+        if self.small is not None:
+            tot += int(self.small.n_accepted.sum().item())
+        return tot
+
+    def reset_counts(self):
+        self.big_accepted.zero_()
+        if self.small is not None:
+            self.small.n_accepted.zero_()
+
+    def flagged_fraction(self):
+        import torch
+        fl = [p[3] for p in self.big_prop]
+        if self.small is not None:
+            fl.append(self.small.prop[3])
+        return float(torch.cat([f.flatten() for f in fl]).ne(0).double().mean().item())

@@ -873,7 +873,7 @@ __host__ __device__ inline WLay wlay(int D, int chi) {
   w.lam = off; off += (int64_t)chi * D * chi;
   w.U1 = off;  off += (int64_t)D * chi * D * chi;
   w.U2 = off;  off += (int64_t)D * D * chi * D * chi;
-  w.U3 = off;  off += (int64_t)D * D * D * D;
+  w.U3 = off;                        // (the warp form needs no U3 buffer)
   w.nT = (off + 1) & ~(int64_t)1;    // keep the int tail 8-byte aligned
   w.nI = K;
   return w;
@@ -1083,7 +1083,7 @@ __global__ void __launch_bounds__(128) sample3d_warp_kernel(Samp3 a) {
   const WLay wl = wlay(D, chi);
   T* ws = reinterpret_cast<T*>(smem3 + (size_t)(threadIdx.x >> 5) * wslice_bytes(wl, sizeof(T)));
   T *J = ws + wl.J, *dv = ws + wl.d, *sm = ws + wl.sm, *tmp = ws + wl.tmp, *lam = ws + wl.lam;
-  T *U1 = ws + wl.U1, *U2 = ws + wl.U2, *U3 = ws + wl.U3;
+  T *U1 = ws + wl.U1, *U2 = ws + wl.U2;
   int* sel = reinterpret_cast<int*>(ws + wl.nT);
   T* base = static_cast<T*>(a.scr) + b * o.total;       // this sample's HBM scratch, contiguous
   T *Bot = base + o.bot, *Top = base + o.top, *W = base + o.w, *R = base + o.R;
@@ -1234,33 +1234,28 @@ __global__ void __launch_bounds__(128) sample3d_warp_kernel(Samp3 a) {
           U2[e] = acc;
         }
         __syncwarp();
-        for (int e = lane; e < dl * du * dd * dr; e += 32) {
-          int t = e;
-          const int r = t % dr; t /= dr;
-          const int d = t % dd; t /= dd;
-          const int u = t % du;
-          const int l = t / du;
-          T acc = 0;
-          for (int c = 0; c < tc; ++c)
-            for (int q = 0; q < qb; ++q)
-              acc += U2[((((int64_t)l * du + u) * tc + c) * dd + d) * qb + q] * Rn[((int64_t)c * dr + r) * qb + q];
-          U3[e] = acc;
-        }
-        __syncwarp();
+        // w(s) = f(s) sum_{l,u,d,r} A[s][u][l][d][r] U3[l][u][d][r], U3 = sum_{c,q} U2 R_{x+1}:
+        // each lane forms its U3 entries on the fly (no U3 buffer)
         T w[2];
-        for (int s = 0; s < 2; ++s) {
-          T acc = 0;
+        {
+          T p0 = 0, p1 = 0;
           for (int e = lane; e < dl * du * dd * dr; e += 32) {
             int t = e;
             const int r = t % dr; t /= dr;
             const int d = t % dd; t /= dd;
             const int u = t % du;
             const int l = t / du;
-            acc += As[pad_index(D, s, u, l, d, r)] * U3[e];
+            T u3 = 0;
+            for (int c = 0; c < tc; ++c)
+              for (int q = 0; q < qb; ++q)
+                u3 += U2[((((int64_t)l * du + u) * tc + c) * dd + d) * qb + q] * Rn[((int64_t)c * dr + r) * qb + q];
+            p0 += As[pad_index(D, 0, u, l, d, r)] * u3;
+            p1 += As[pad_index(D, 1, u, l, d, r)] * u3;
           }
-          acc = wsum(acc);
-          w[s] = acc * field3<T>(a, z, y, x, s, sp);
-          if (!(w[s] > 0)) w[s] = 0;
+          w[0] = wsum(p0) * field3<T>(a, z, y, x, 0, sp);
+          w[1] = wsum(p1) * field3<T>(a, z, y, x, 1, sp);
+          if (!(w[0] > 0)) w[0] = 0;
+          if (!(w[1] > 0)) w[1] = 0;
         }
         const T tot = w[0] + w[1];
         const bool bad = !(tot > 0) || !isfinite((double)tot);

@@ -218,3 +218,28 @@ def test_batch_balance_is_a_fraction(B):
     run.plan.sample(run.prop)
     eff, span = run.plan.balance()
     assert 0.0 < eff <= 1.0 and span > 0.0
+
+
+def test_mixed_runner_matches_single_instance_calls(B):
+    """The per-chi-class runner: its tensor-core instances evolve exactly as the
+    single-instance BF16 sample + MH calls with the documented counters, and its FP32
+    instances as their own persistent plan."""
+    from paper_2104_13264_gb300 import batched
+    insts = [instances.ea_gauss(8, 8, 2.0, 4, seed=1), instances.ea_gauss(10, 10, 2.0, 32, seed=2),
+             instances.ea_gauss(6, 9, 2.0, 8, seed=3), instances.ea_gauss(12, 12, 2.0, 32, seed=4)]
+    run = batched.MixedRunner(insts, 256, 8, tc_chi=32, seed=5, tune=False)
+    assert run.big_idx == [1, 3] and run.small_idx == [0, 2]
+    start = [tuple(t.clone() for t in ch) for ch in run.big_chain]
+    for _ in range(2):
+        run.step()
+    torch.cuda.synchronize()
+    for j, i in enumerate(run.big_idx):
+        e = run.big_envs[j]
+        ch = start[j]
+        idx = len(run.small_idx) + j
+        for k in range(2):
+            sp, lq, E, _ = B.sample(e, 256, seed=5, sample_offset=(idx << 40) + k * 256, precision="bf16")
+            B.mh_step(e, 8, 32, (sp, lq, E), ch, seed=5, step_offset=(idx << 40) + k * 32)
+        torch.cuda.synchronize()
+        assert torch.equal(ch[0], run.big_chain[j][0]) and torch.equal(ch[1], run.big_chain[j][1])
+    assert run.n_accepted() > 0
