@@ -547,7 +547,7 @@ struct Samp3 {
 
 struct Lay3 {   // offsets (in elements) of one sample's scratch
   int64_t capS, capW;
-  int64_t bot, top, w, J, d, sm, tmp, R, lam, U1, U2, U3, total;
+  int64_t bot, top, w, J, d, sm, tmp, R, lam, U1, U2, total;
 };
 
 __host__ __device__ inline Lay3 lay3(int Lx, int Ly, int D, int chi) {
@@ -567,7 +567,6 @@ __host__ __device__ inline Lay3 lay3(int Lx, int Ly, int D, int chi) {
   o.lam = off; off += o.capS;
   o.U1 = off;  off += (int64_t)D * chi * D * chi;
   o.U2 = off;  off += (int64_t)D * D * chi * D * chi;
-  o.U3 = off;  off += (int64_t)D * D * D * D;
   o.total = off;
   return o;
 }
@@ -594,7 +593,7 @@ __global__ void __launch_bounds__(128, 4) sample3d_kernel(Samp3 a) {
   const V<T> base{static_cast<T*>(a.scr) + b, a.Bc};
   const V<T> Bot = base.at(o.bot), Top = base.at(o.top), W = base.at(o.w), J = base.at(o.J), dv = base.at(o.d);
   const V<T> sm = base.at(o.sm), tmp = base.at(o.tmp), R = base.at(o.R), lam = base.at(o.lam);
-  const V<T> U1 = base.at(o.U1), U2 = base.at(o.U2), U3 = base.at(o.U3);
+  const V<T> U1 = base.at(o.U1), U2 = base.at(o.U2);
   const V<int32_t> botb{a.iscr + b, a.Bc};
   const T* A = static_cast<const T*>(a.A);
   const int64_t site_sz = 2LL * D * D * D * D;
@@ -725,27 +724,27 @@ __global__ void __launch_bounds__(128, 4) sample3d_kernel(Samp3 a) {
                     acc += U1[(((int64_t)l * pb + p) * du + u) * tc + c] * Bx[((int64_t)p * dd + d) * qb + q];
                   U2[((((int64_t)l * du + u) * tc + c) * dd + d) * qb + q] = acc;
                 }
-        // U3[l][u][d][r] = sum_{c,q} U2[l][u][c][d][q] R_{x+1}[c][r][q]
-        for (int l = 0; l < dl; ++l)
-          for (int u = 0; u < du; ++u)
-            for (int d = 0; d < dd; ++d)
-              for (int r = 0; r < dr; ++r) {
-                T acc = 0;
-                for (int c = 0; c < tc; ++c)
-                  for (int q = 0; q < qb; ++q)
-                    acc += U2[((((int64_t)l * du + u) * tc + c) * dd + d) * qb + q] * Rn[((int64_t)c * dr + r) * qb + q];
-                U3[(((int64_t)l * du + u) * dd + d) * dr + r] = acc;
-              }
+        // w(s) = f(s) sum_{l,u,d,r} A[s][u][l][d][r] U3[l][u][d][r] with
+        // U3[l][u][d][r] = sum_{c,q} U2[l][u][c][d][q] R_{x+1}[c][r][q], each U3 entry formed
+        // on the fly (it never goes to the scratch)
         T w[2];
-        for (int s = 0; s < 2; ++s) {
-          T acc = 0;
-          for (int u = 0; u < du; ++u)
-            for (int l = 0; l < dl; ++l)
+        {
+          T p0 = 0, p1 = 0;
+          for (int l = 0; l < dl; ++l)
+            for (int u = 0; u < du; ++u)
               for (int d = 0; d < dd; ++d)
-                for (int r = 0; r < dr; ++r)
-                  acc += As[pad_index(D, s, u, l, d, r)] * U3[(((int64_t)l * du + u) * dd + d) * dr + r];
-          w[s] = acc * field3<T>(a, z, y, x, s, sp);
-          if (!(w[s] > 0)) w[s] = 0;
+                for (int r = 0; r < dr; ++r) {
+                  T u3 = 0;
+                  for (int c = 0; c < tc; ++c)
+                    for (int q = 0; q < qb; ++q)
+                      u3 += U2[((((int64_t)l * du + u) * tc + c) * dd + d) * qb + q] * Rn[((int64_t)c * dr + r) * qb + q];
+                  p0 += As[pad_index(D, 0, u, l, d, r)] * u3;
+                  p1 += As[pad_index(D, 1, u, l, d, r)] * u3;
+                }
+          w[0] = p0 * field3<T>(a, z, y, x, 0, sp);
+          w[1] = p1 * field3<T>(a, z, y, x, 1, sp);
+          if (!(w[0] > 0)) w[0] = 0;
+          if (!(w[1] > 0)) w[1] = 0;
         }
         const T tot = w[0] + w[1];
         const bool bad = !(tot > 0) || !isfinite((double)tot);
@@ -860,7 +859,7 @@ __device__ __forceinline__ T wmax(T v) {
 }
 
 struct WLay {   // per-warp shared-memory slice (elements of T, then ints)
-  int64_t J, d, sm, tmp, lam, U1, U2, U3, nT, nI;
+  int64_t J, d, sm, tmp, lam, U1, U2, nT, nI;
 };
 __host__ __device__ inline WLay wlay(int D, int chi) {
   WLay w;
@@ -873,7 +872,6 @@ __host__ __device__ inline WLay wlay(int D, int chi) {
   w.lam = off; off += (int64_t)chi * D * chi;
   w.U1 = off;  off += (int64_t)D * chi * D * chi;
   w.U2 = off;  off += (int64_t)D * D * chi * D * chi;
-  w.U3 = off;                        // (the warp form needs no U3 buffer)
   w.nT = (off + 1) & ~(int64_t)1;    // keep the int tail 8-byte aligned
   w.nI = K;
   return w;
