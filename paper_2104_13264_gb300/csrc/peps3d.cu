@@ -25,6 +25,7 @@
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
+#include <string.h>
 
 #include <new>
 
@@ -835,24 +836,26 @@ __global__ void __launch_bounds__(128, 4) sample3d_kernel(Samp3 a) {
 
 
 // ---------------------------------------------------------------------------
-// Sampler, one warp per sample (larger bonds).  The same algorithm and arithmetic order
-// per output element as sample3d_kernel; lane l owns the entries x = l mod 32 of every
-// vector it updates, so the elementwise steps need no synchronisation, and only the
-// scalars (dots, norms, maxima) go through warp reductions.  The small QR / SVD matrices
+// Sampler, one group of G lanes per sample (G = 8, 16 or 32: larger bonds).  The same
+// algorithm and arithmetic order per output element as sample3d_kernel; lane l owns the
+// entries x = l mod G of every vector it updates, so the elementwise steps need no
+// synchronisation, and only the scalars (dots, norms, maxima) go through reductions over
+// the group.  Samples in one warp may take different numbers of Jacobi sweeps, so every
+// shuffle and __syncwarp names the group's own lanes.  The small QR / SVD matrices
 // and the sandwich buffers live in this warp's slice of shared memory; the MPS being
 // compressed, the boundaries and the right vectors stay in HBM, contiguous per sample.
 // ---------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ T wsum(T v) {
+template <int G, typename T>
+__device__ __forceinline__ T wsum(T v, unsigned gm) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(gm, v, o);
   return v;
 }
-template <typename T>
-__device__ __forceinline__ T wmax(T v) {
+template <int G, typename T>
+__device__ __forceinline__ T wmax(T v, unsigned gm) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const T u = __shfl_xor_sync(0xffffffffu, v, o);
+  for (int o = G / 2; o > 0; o >>= 1) {
+    const T u = __shfl_xor_sync(gm, v, o);
     v = u > v ? u : v;
   }
   return v;
@@ -881,19 +884,19 @@ __host__ __device__ inline size_t wslice_bytes(const WLay& w, size_t esz) {
   return ((size_t)w.nT * esz + (size_t)w.nI * sizeof(int) + 15) & ~(size_t)15;
 }
 
-template <typename T>
-__device__ bool orth_rows_w(T* J, int m, int n, T* d, int lane) {
+template <int G, typename T>
+__device__ bool orth_rows_w(T* J, int m, int n, T* d, int lane, unsigned gm) {
   bool converged = false;
   for (int sweep = 0; sweep < kSweeps3 && !converged; ++sweep) {
     T dmax = 0;
     for (int i = 0; i < m; ++i) {
       T s = 0;
-      for (int x = lane; x < n; x += 32) s += J[(int64_t)i * n + x] * J[(int64_t)i * n + x];
-      s = wsum(s);
+      for (int x = lane; x < n; x += G) s += J[(int64_t)i * n + x] * J[(int64_t)i * n + x];
+      s = wsum<G>(s, gm);
       if (lane == 0) d[i] = s;
       dmax = s > dmax ? s : dmax;
     }
-    __syncwarp();
+    __syncwarp(gm);
     const T dnull = Tol3<T>::null * Tol3<T>::null * dmax;
     bool rotated = false;
     for (int p = 0; p + 1 < m; ++p) {
@@ -901,24 +904,24 @@ __device__ bool orth_rows_w(T* J, int m, int n, T* d, int lane) {
         const T al = d[p], be = d[q];
         if (al <= dnull || be <= dnull) continue;
         T ga = 0;
-        for (int x = lane; x < n; x += 32) ga += J[(int64_t)p * n + x] * J[(int64_t)q * n + x];
-        ga = wsum(ga);
+        for (int x = lane; x < n; x += G) ga += J[(int64_t)p * n + x] * J[(int64_t)q * n + x];
+        ga = wsum<G>(ga, gm);
         if (!(ga * ga > Tol3<T>::rot * Tol3<T>::rot * al * be)) continue;
         const T zeta = (be - al) / (T(2) * ga);
         const T az = zeta < 0 ? -zeta : zeta;
         const T t = az > Tol3<T>::big ? T(0.5) / zeta : (zeta >= 0 ? T(1) : T(-1)) / (az + sqrt(T(1) + zeta * zeta));
         const T c = T(1) / sqrt(T(1) + t * t), sn = c * t;
-        for (int x = lane; x < n; x += 32) {
+        for (int x = lane; x < n; x += G) {
           const T u = J[(int64_t)p * n + x], v = J[(int64_t)q * n + x];
           J[(int64_t)p * n + x] = c * u - sn * v;
           J[(int64_t)q * n + x] = sn * u + c * v;
         }
-        __syncwarp();
+        __syncwarp(gm);
         if (lane == 0) {
           d[p] = al - t * ga;
           d[q] = be + t * ga;
         }
-        __syncwarp();
+        __syncwarp(gm);
         rotated = true;
       }
     }
@@ -926,17 +929,17 @@ __device__ bool orth_rows_w(T* J, int m, int n, T* d, int lane) {
   }
   for (int i = 0; i < m; ++i) {
     T s = 0;
-    for (int x = lane; x < n; x += 32) s += J[(int64_t)i * n + x] * J[(int64_t)i * n + x];
-    s = wsum(s);
+    for (int x = lane; x < n; x += G) s += J[(int64_t)i * n + x] * J[(int64_t)i * n + x];
+    s = wsum<G>(s, gm);
     if (lane == 0) d[i] = sqrt(s);
   }
-  __syncwarp();
+  __syncwarp(gm);
   return converged;
 }
 
-template <typename T>
+template <int G, typename T>
 __device__ int mps_compress_w(T* M, int64_t cap, int ns, int* dl, const int* pp, int* dr, int kmax, T* J, T* d,
-                              T* sm, T* tmp, int* sel, int lane, double* logs) {
+                              T* sm, T* tmp, int* sel, int lane, unsigned gm, double* logs) {
   int err = 0;
   double lg = 0.0;
   for (int i = 0; i + 1 < ns; ++i) {
@@ -944,62 +947,62 @@ __device__ int mps_compress_w(T* M, int64_t cap, int ns, int* dl, const int* pp,
     T* Mi = M + i * cap;
     const int k = len < b ? len : b;
     if (b > kMaxRows3) return TNMC_E_NUMERIC;
-    for (int e = lane; e < k * b; e += 32) sm[e] = T(0);
-    __syncwarp();
+    for (int e = lane; e < k * b; e += G) sm[e] = T(0);
+    __syncwarp(gm);
     int acc = 0;
     for (int j = 0; j < b; ++j) {
       T nx = 0;
-      for (int x = lane; x < len; x += 32) {
+      for (int x = lane; x < len; x += G) {
         const T v = Mi[(int64_t)x * b + j];
         tmp[x] = v;
         nx += v * v;
       }
-      nx = wsum(nx);
+      nx = wsum<G>(nx, gm);
       for (int pass = 0; pass < 2; ++pass)
         for (int q = 0; q < acc; ++q) {
           T r = 0;
-          for (int x = lane; x < len; x += 32) r += J[(int64_t)q * len + x] * tmp[x];
-          r = wsum(r);
-          for (int x = lane; x < len; x += 32) tmp[x] -= r * J[(int64_t)q * len + x];
+          for (int x = lane; x < len; x += G) r += J[(int64_t)q * len + x] * tmp[x];
+          r = wsum<G>(r, gm);
+          for (int x = lane; x < len; x += G) tmp[x] -= r * J[(int64_t)q * len + x];
           if (lane == 0) sm[(int64_t)q * b + j] += r;
         }
       T nv = 0;
-      for (int x = lane; x < len; x += 32) nv += tmp[x] * tmp[x];
-      nv = sqrt(wsum(nv));
+      for (int x = lane; x < len; x += G) nv += tmp[x] * tmp[x];
+      nv = sqrt(wsum<G>(nv, gm));
       if (acc < k && nv > Tol3<T>::qr * sqrt(nx) && nv > 0) {
         const T inv = T(1) / nv;
-        for (int x = lane; x < len; x += 32) J[(int64_t)acc * len + x] = tmp[x] * inv;
+        for (int x = lane; x < len; x += G) J[(int64_t)acc * len + x] = tmp[x] * inv;
         if (lane == 0) sm[(int64_t)acc * b + j] = nv;
         ++acc;
       }
     }
     for (int q = acc; q < k; ++q)
-      for (int x = lane; x < len; x += 32) J[(int64_t)q * len + x] = T(0);
-    __syncwarp();
+      for (int x = lane; x < len; x += G) J[(int64_t)q * len + x] = T(0);
+    __syncwarp(gm);
     T sc = 0;
-    for (int e = lane; e < k * b; e += 32) {
+    for (int e = lane; e < k * b; e += G) {
       const T aa = sm[e] < 0 ? -sm[e] : sm[e];
       sc = aa > sc ? aa : sc;
     }
-    sc = wmax(sc);
+    sc = wmax<G>(sc, gm);
     if (!(sc > 0) || !isfinite((double)sc)) return TNMC_E_NUMERIC;
     lg += log((double)sc);
-    for (int e = lane; e < k * len; e += 32) {
+    for (int e = lane; e < k * len; e += G) {
       const int x = e / k, q = e % k;
       Mi[e] = J[(int64_t)q * len + x];
     }
     T* Mn = M + (i + 1) * cap;
     const int rest = pp[i + 1] * dr[i + 1];
     const T isc = T(1) / sc;
-    for (int e = lane; e < k * rest; e += 32) {
+    for (int e = lane; e < k * rest; e += G) {
       const int j = e / rest, y = e % rest;
       T accv = 0;
       for (int c = 0; c < b; ++c) accv += sm[(int64_t)j * b + c] * Mn[(int64_t)c * rest + y];
       tmp[e] = accv * isc;
     }
-    __syncwarp();
-    for (int e = lane; e < k * rest; e += 32) Mn[e] = tmp[e];
-    __syncwarp();
+    __syncwarp(gm);
+    for (int e = lane; e < k * rest; e += G) Mn[e] = tmp[e];
+    __syncwarp(gm);
     dr[i] = k;
     dl[i + 1] = k;
   }
@@ -1007,9 +1010,9 @@ __device__ int mps_compress_w(T* M, int64_t cap, int ns, int* dl, const int* pp,
     const int a = dl[i], p = pp[i], b = dr[i], len = p * b;
     T* Mi = M + i * cap;
     if (a > kMaxRows3) return TNMC_E_NUMERIC;
-    for (int e = lane; e < a * len; e += 32) J[e] = Mi[e];
-    __syncwarp();
-    if (!orth_rows_w(J, a, len, d, lane)) err = TNMC_E_NUMERIC;
+    for (int e = lane; e < a * len; e += G) J[e] = Mi[e];
+    __syncwarp(gm);
+    if (!orth_rows_w<G>(J, a, len, d, lane, gm)) err = TNMC_E_NUMERIC;
     int k = a < len ? a : len;
     k = kmax < k ? kmax : k;
     if (lane == 0) {
@@ -1020,66 +1023,68 @@ __device__ int mps_compress_w(T* M, int64_t cap, int ns, int* dl, const int* pp,
         if (rank < k) sel[rank] = r;
       }
     }
-    __syncwarp();
+    __syncwarp(gm);
     const T smax = d[sel[0]];
     if (!(smax > 0) || !isfinite((double)smax)) return TNMC_E_NUMERIC;
-    for (int e = lane; e < k * len; e += 32) {
+    for (int e = lane; e < k * len; e += G) {
       const int j = e / len, y = e % len;
       const T nj = d[sel[j]];
       tmp[e] = nj > Tol3<T>::null * smax ? J[(int64_t)sel[j] * len + y] / nj : T(0);
     }
-    __syncwarp();
+    __syncwarp(gm);
     const T is = T(1) / smax;
-    for (int e = lane; e < a * k; e += 32) {
+    for (int e = lane; e < a * k; e += G) {
       const int r = e / k, j = e % k;
       T accv = 0;
       for (int y = 0; y < len; ++y) accv += Mi[(int64_t)r * len + y] * tmp[(int64_t)j * len + y];
       sm[e] = accv * is;
     }
-    __syncwarp();
+    __syncwarp(gm);
     lg += log((double)smax);
-    for (int e = lane; e < k * len; e += 32) Mi[e] = tmp[e];
+    for (int e = lane; e < k * len; e += G) Mi[e] = tmp[e];
     T* Mp = M + (i - 1) * cap;
     const int rows = dl[i - 1] * pp[i - 1];
-    __syncwarp();
-    for (int e = lane; e < rows * k; e += 32) {
+    __syncwarp(gm);
+    for (int e = lane; e < rows * k; e += G) {
       const int z = e / k, j = e % k;
       T accv = 0;
       for (int r = 0; r < a; ++r) accv += Mp[(int64_t)z * a + r] * sm[(int64_t)r * k + j];
       tmp[e] = accv;
     }
-    __syncwarp();
-    for (int e = lane; e < rows * k; e += 32) Mp[e] = tmp[e];
-    __syncwarp();
+    __syncwarp(gm);
+    for (int e = lane; e < rows * k; e += G) Mp[e] = tmp[e];
+    __syncwarp(gm);
     dl[i] = k;
     dr[i - 1] = k;
   }
   {
     const int n0 = dl[0] * pp[0] * dr[0];
     T s = 0;
-    for (int e = lane; e < n0; e += 32) s += M[e] * M[e];
-    const T nrm = sqrt(wsum(s));
+    for (int e = lane; e < n0; e += G) s += M[e] * M[e];
+    const T nrm = sqrt(wsum<G>(s, gm));
     if (!(nrm > 0) || !isfinite((double)nrm)) return TNMC_E_NUMERIC;
     const T inv = T(1) / nrm;
-    for (int e = lane; e < n0; e += 32) M[e] *= inv;
-    __syncwarp();
+    for (int e = lane; e < n0; e += G) M[e] *= inv;
+    __syncwarp(gm);
     lg += log((double)nrm);
   }
   *logs = lg;
   return err;
 }
 
-template <typename T>
+template <typename T, int G>
 __global__ void __launch_bounds__(128) sample3d_warp_kernel(Samp3 a) {
   extern __shared__ unsigned char smem3[];
-  const int lane = threadIdx.x & 31;
-  const int64_t b = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;   // one sample per warp
-  if (b >= a.Bc) return;      // warp-uniform
+  const int lane = threadIdx.x & (G - 1);
+  // the G lanes of one sample: their mask within the warp
+  const unsigned gm = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
+  const int64_t b = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;   // one sample per group of G lanes
+  if (b >= a.Bc) return;      // uniform within the group
   const int64_t g = a.b0 + b;
   const int Lx = a.Lx, Ly = a.Ly, Lz = a.Lz, D = a.D, chi = a.chi;
   const Lay3 o = lay3(Lx, Ly, D, chi);
   const WLay wl = wlay(D, chi);
-  T* ws = reinterpret_cast<T*>(smem3 + (size_t)(threadIdx.x >> 5) * wslice_bytes(wl, sizeof(T)));
+  T* ws = reinterpret_cast<T*>(smem3 + (size_t)(threadIdx.x / G) * wslice_bytes(wl, sizeof(T)));
   T *J = ws + wl.J, *dv = ws + wl.d, *sm = ws + wl.sm, *tmp = ws + wl.tmp, *lam = ws + wl.lam;
   T *U1 = ws + wl.U1, *U2 = ws + wl.U2;
   int* sel = reinterpret_cast<int*>(ws + wl.nT);
@@ -1096,9 +1101,9 @@ __global__ void __launch_bounds__(128) sample3d_warp_kernel(Samp3 a) {
   for (int z = 0; z < Lz; ++z) {
     auto Aof = [&](int y, int x) { return A + (((int64_t)z * Ly + y) * Lx + x) * site_sz; };
     auto dimof = [&](int y, int x, int k) { return (int)a.dims[(((int64_t)z * Ly + y) * Lx + x) * 4 + k]; };
-    for (int x = lane; x <= Lx; x += 32) botb[(int64_t)(Ly - 1) * (Lx + 1) + x] = 1;
-    for (int x = lane; x < Lx; x += 32) Bot[((int64_t)(Ly - 1) * Lx + x) * o.capS] = T(1);
-    __syncwarp();
+    for (int x = lane; x <= Lx; x += G) botb[(int64_t)(Ly - 1) * (Lx + 1) + x] = 1;
+    for (int x = lane; x < Lx; x += G) Bot[((int64_t)(Ly - 1) * Lx + x) * o.capS] = T(1);
+    __syncwarp(gm);
     for (int y = Ly - 2; y >= 0; --y) {
       for (int x = 0; x < Lx; ++x) {
         const T* As = Aof(y + 1, x);
@@ -1109,7 +1114,7 @@ __global__ void __launch_bounds__(128) sample3d_warp_kernel(Samp3 a) {
         T* Wx = W + x * o.capW;
         const int ncol = dr * br;
         const int total = dl * bl * du * ncol;
-        for (int e = lane; e < total; e += 32) {
+        for (int e = lane; e < total; e += G) {
           int t = e;
           const int q = t % br; t /= br;
           const int r = t % dr; t /= dr;
@@ -1127,27 +1132,27 @@ __global__ void __launch_bounds__(128) sample3d_warp_kernel(Samp3 a) {
         wp[x] = du;
         wr[x] = ncol;
       }
-      __syncwarp();
+      __syncwarp(gm);
       double lg;
-      const int e = mps_compress_w(W, o.capW, Lx, wlv, wp, wr, chi, J, dv, sm, tmp, sel, lane, &lg);
+      const int e = mps_compress_w<G>(W, o.capW, Lx, wlv, wp, wr, chi, J, dv, sm, tmp, sel, lane, gm, &lg);
       err = err ? err : e;
       for (int x = 0; x < Lx; ++x) {
         T* Bd = Bot + ((int64_t)y * Lx + x) * o.capS;
         const T* Wx = W + x * o.capW;
         const int n = wlv[x] * wp[x] * wr[x];
-        for (int i = lane; i < n; i += 32) Bd[i] = Wx[i];
+        for (int i = lane; i < n; i += G) Bd[i] = Wx[i];
         if (lane == 0) botb[(int64_t)y * (Lx + 1) + x] = wlv[x];
       }
       if (lane == 0) botb[(int64_t)y * (Lx + 1) + Lx] = 1;
-      __syncwarp();
+      __syncwarp(gm);
     }
     for (int x = 0; x <= Lx; ++x) tb[x] = 1;
-    for (int x = lane; x < Lx; x += 32) Top[x * o.capS] = T(1);
-    __syncwarp();
+    for (int x = lane; x < Lx; x += G) Top[x * o.capS] = T(1);
+    __syncwarp(gm);
     for (int y = 0; y < Ly; ++y) {
       const int64_t brow = (int64_t)y * (Lx + 1);
       if (lane == 0) R[(int64_t)Lx * o.capS] = T(1);
-      __syncwarp();
+      __syncwarp(gm);
       for (int x = Lx - 1; x >= 1; --x) {
         const T* As = Aof(y, x);
         const int du = dimof(y, x, 0), dl = dimof(y, x, 1), dd = dimof(y, x, 2), dr = dimof(y, x, 3);
@@ -1156,7 +1161,7 @@ __global__ void __launch_bounds__(128) sample3d_warp_kernel(Samp3 a) {
         const T *Tx = Top + x * o.capS, *Bx = Bot + ((int64_t)y * Lx + x) * o.capS;
         const T* Rn = R + (int64_t)(x + 1) * o.capS;
         T* Rx = R + (int64_t)x * o.capS;
-        for (int e = lane; e < ta * du * dr * qb; e += 32) {
+        for (int e = lane; e < ta * du * dr * qb; e += G) {
           int t = e;
           const int q = t % qb; t /= qb;
           const int r = t % dr; t /= dr;
@@ -1166,8 +1171,8 @@ __global__ void __launch_bounds__(128) sample3d_warp_kernel(Samp3 a) {
           for (int c = 0; c < tc; ++c) acc += Tx[((int64_t)aa * du + u) * tc + c] * Rn[((int64_t)c * dr + r) * qb + q];
           U1[e] = acc;
         }
-        __syncwarp();
-        for (int e = lane; e < ta * dl * dd * qb; e += 32) {
+        __syncwarp(gm);
+        for (int e = lane; e < ta * dl * dd * qb; e += G) {
           int t = e;
           const int q = t % qb; t /= qb;
           const int d = t % dd; t /= dd;
@@ -1181,9 +1186,9 @@ __global__ void __launch_bounds__(128) sample3d_warp_kernel(Samp3 a) {
             }
           U2[e] = acc;
         }
-        __syncwarp();
+        __syncwarp(gm);
         T mx = 0;
-        for (int e = lane; e < ta * dl * pb; e += 32) {
+        for (int e = lane; e < ta * dl * pb; e += G) {
           const int p = e % pb, l = (e / pb) % dl, aa = e / (pb * dl);
           T acc = 0;
           for (int d = 0; d < dd; ++d)
@@ -1192,23 +1197,23 @@ __global__ void __launch_bounds__(128) sample3d_warp_kernel(Samp3 a) {
           Rx[e] = acc;
           mx = absT(acc) > mx ? absT(acc) : mx;
         }
-        mx = wmax(mx);
-        __syncwarp();
+        mx = wmax<G>(mx, gm);
+        __syncwarp(gm);
         if (mx > 0 && isfinite((double)mx)) {
           const T inv = T(1) / mx;
-          for (int e = lane; e < ta * dl * pb; e += 32) Rx[e] *= inv;
+          for (int e = lane; e < ta * dl * pb; e += G) Rx[e] *= inv;
         }
-        __syncwarp();
+        __syncwarp(gm);
       }
       if (lane == 0) lam[0] = T(1);
-      __syncwarp();
+      __syncwarp(gm);
       for (int x = 0; x < Lx; ++x) {
         const T* As = Aof(y, x);
         const int du = dimof(y, x, 0), dl = dimof(y, x, 1), dd = dimof(y, x, 2), dr = dimof(y, x, 3);
         const int ta = tb[x], tc = tb[x + 1], pb = botb[brow + x], qb = botb[brow + x + 1];
         const T *Tx = Top + x * o.capS, *Bx = Bot + ((int64_t)y * Lx + x) * o.capS;
         const T* Rn = R + (int64_t)(x + 1) * o.capS;
-        for (int e = lane; e < dl * pb * du * tc; e += 32) {
+        for (int e = lane; e < dl * pb * du * tc; e += G) {
           int t = e;
           const int c = t % tc; t /= tc;
           const int u = t % du; t /= du;
@@ -1218,8 +1223,8 @@ __global__ void __launch_bounds__(128) sample3d_warp_kernel(Samp3 a) {
           for (int aa = 0; aa < ta; ++aa) acc += lam[((int64_t)aa * dl + l) * pb + p] * Tx[((int64_t)aa * du + u) * tc + c];
           U1[e] = acc;
         }
-        __syncwarp();
-        for (int e = lane; e < dl * du * tc * dd * qb; e += 32) {
+        __syncwarp(gm);
+        for (int e = lane; e < dl * du * tc * dd * qb; e += G) {
           int t = e;
           const int q = t % qb; t /= qb;
           const int d = t % dd; t /= dd;
@@ -1231,13 +1236,13 @@ __global__ void __launch_bounds__(128) sample3d_warp_kernel(Samp3 a) {
             acc += U1[(((int64_t)l * pb + p) * du + u) * tc + c] * Bx[((int64_t)p * dd + d) * qb + q];
           U2[e] = acc;
         }
-        __syncwarp();
+        __syncwarp(gm);
         // w(s) = f(s) sum_{l,u,d,r} A[s][u][l][d][r] U3[l][u][d][r], U3 = sum_{c,q} U2 R_{x+1}:
         // each lane forms its U3 entries on the fly (no U3 buffer)
         T w[2];
         {
           T p0 = 0, p1 = 0;
-          for (int e = lane; e < dl * du * dd * dr; e += 32) {
+          for (int e = lane; e < dl * du * dd * dr; e += G) {
             int t = e;
             const int r = t % dr; t /= dr;
             const int d = t % dd; t /= dd;
@@ -1250,8 +1255,8 @@ __global__ void __launch_bounds__(128) sample3d_warp_kernel(Samp3 a) {
             p0 += As[pad_index(D, 0, u, l, d, r)] * u3;
             p1 += As[pad_index(D, 1, u, l, d, r)] * u3;
           }
-          w[0] = wsum(p0) * field3<T>(a, z, y, x, 0, sp);
-          w[1] = wsum(p1) * field3<T>(a, z, y, x, 1, sp);
+          w[0] = wsum<G>(p0, gm) * field3<T>(a, z, y, x, 0, sp);
+          w[1] = wsum<G>(p1, gm) * field3<T>(a, z, y, x, 1, sp);
           if (!(w[0] > 0)) w[0] = 0;
           if (!(w[1] > 0)) w[1] = 0;
         }
@@ -1265,16 +1270,16 @@ __global__ void __launch_bounds__(128) sample3d_warp_kernel(Samp3 a) {
           plus = sp[si] > 0;
         } else {
           plus = draw_plus(pplus, draw_word(a.seed, si, sample));
-          __syncwarp();
+          __syncwarp(gm);
           if (lane == 0) sp[si] = plus ? 1 : -1;
         }
-        __syncwarp();
+        __syncwarp(gm);
         lq += log((double)(plus ? pplus : pminus));
         if (bad) flag = TNMC_FLAG_NUMERIC;
         const int s = plus ? 1 : 0;
         const T fs = field3<T>(a, z, y, x, s, sp);
         T mx = 0;
-        for (int e = lane; e < tc * dr * qb; e += 32) {
+        for (int e = lane; e < tc * dr * qb; e += G) {
           const int q = e % qb, r = (e / qb) % dr, c = e / (qb * dr);
           T acc = 0;
           for (int l = 0; l < dl; ++l)
@@ -1285,11 +1290,11 @@ __global__ void __launch_bounds__(128) sample3d_warp_kernel(Samp3 a) {
           tmp[e] = acc;
           mx = absT(acc) > mx ? absT(acc) : mx;
         }
-        mx = wmax(mx);
-        __syncwarp();
+        mx = wmax<G>(mx, gm);
+        __syncwarp(gm);
         const T inv = (mx > 0 && isfinite((double)mx)) ? T(1) / mx : T(1);
-        for (int i = lane; i < tc * dr * qb; i += 32) lam[i] = tmp[i] * inv;
-        __syncwarp();
+        for (int i = lane; i < tc * dr * qb; i += G) lam[i] = tmp[i] * inv;
+        __syncwarp(gm);
       }
       if (y + 1 < Ly) {
         for (int x = 0; x < Lx; ++x) {
@@ -1301,7 +1306,7 @@ __global__ void __launch_bounds__(128) sample3d_warp_kernel(Samp3 a) {
           const T* Tx = Top + x * o.capS;
           T* Wx = W + x * o.capW;
           const int ncol = tc * dr;
-          for (int e = lane; e < ta * dl * dd * tc * dr; e += 32) {
+          for (int e = lane; e < ta * dl * dd * tc * dr; e += G) {
             int t = e;
             const int r = t % dr; t /= dr;
             const int c = t % tc; t /= tc;
@@ -1316,19 +1321,19 @@ __global__ void __launch_bounds__(128) sample3d_warp_kernel(Samp3 a) {
           wp[x] = dd;
           wr[x] = ncol;
         }
-        __syncwarp();
+        __syncwarp(gm);
         double lg;
-        const int e = mps_compress_w(W, o.capW, Lx, wlv, wp, wr, chi, J, dv, sm, tmp, sel, lane, &lg);
+        const int e = mps_compress_w<G>(W, o.capW, Lx, wlv, wp, wr, chi, J, dv, sm, tmp, sel, lane, gm, &lg);
         err = err ? err : e;
         for (int x = 0; x < Lx; ++x) {
           T* Tx = Top + x * o.capS;
           const T* Wx = W + x * o.capW;
           const int n = wlv[x] * wp[x] * wr[x];
-          for (int i = lane; i < n; i += 32) Tx[i] = Wx[i];
+          for (int i = lane; i < n; i += G) Tx[i] = Wx[i];
           tb[x] = wlv[x];
         }
         tb[Lx] = 1;
-        __syncwarp();
+        __syncwarp(gm);
       }
     }
   }
@@ -1364,6 +1369,18 @@ __global__ void __launch_bounds__(128) sample3d_warp_kernel(Samp3 a) {
   } while (0)
 
 static size_t align256_3(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// One launch of the group-per-sample sampler: spb samples (spb G threads) per CTA.
+template <typename T, int G>
+static tnmc_status launch_group(const tnmc::Samp3& a, int spb, size_t wbytes, cudaStream_t s) {
+  const size_t smem = (size_t)spb * wbytes;
+  TNMC_CUDA_TRY(cudaFuncSetAttribute(tnmc::sample3d_warp_kernel<T, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+  const unsigned blocks = (unsigned)((a.Bc + spb - 1) / spb);
+  tnmc::sample3d_warp_kernel<T, G><<<blocks, spb * G, smem, s>>>(a);
+  TNMC_CUDA_TRY(cudaGetLastError());
+  return TNMC_OK;
+}
 
 extern "C" {
 
@@ -1589,47 +1606,50 @@ static tnmc_status run3d(const tnmc3d_env* env, int precision, int64_t B, uint64
   a.flags = flags;
   a.scr = scr;
   a.iscr = reinterpret_cast<int32_t*>(scr + fbytes);
-  // one warp per sample for the larger bonds (its QR / SVD matrices in shared memory), one
-  // thread per sample for the small ones, where most lanes of a warp-wide step would idle
-  // (measured: the warp form is 3x slower at (D chi) = 8 and 1.4x faster at 16);
-  // TNMC_3D_KERNEL=thread|warp overrides (testing)
+  // one warp per sample from D chi = 16 (its QR / SVD matrices in shared memory), one
+  // thread per sample below.  Measured on the 16^3 bond-basis (2, 2) line (D chi = 8):
+  // one thread 15.9 s per step, groups of 8 lanes 29.3 s, of 16 lanes 41.5 s (the per-step
+  // reductions and syncs cost more than the lanes gain on 8-wide vectors); at D chi = 16 the
+  // warp form is the faster one.  TNMC_3D_KERNEL=thread|warp|group8|group16 overrides.
   const WLay wl = wlay(env->Ds, env->chi);
   const size_t wbytes = wslice_bytes(wl, esz);
   int dev = 0, max_optin = 0;
   TNMC_CUDA_TRY(cudaGetDevice(&dev));
   TNMC_CUDA_TRY(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  int wpb = (int)((size_t)max_optin / wbytes);
-  wpb = wpb > 4 ? 4 : wpb;
-  bool warp = (int64_t)env->Ds * env->chi >= 16 && wpb >= 1;
+  const int64_t K = (int64_t)env->Ds * env->chi;
+  int G = K >= 16 ? 32 : 0;
   const char* force = getenv("TNMC_3D_KERNEL");
-  if (force && force[0] == 't') warp = false;
-  if (force && force[0] == 'w' && wpb >= 1) warp = true;
-  if (warp) {
-    const size_t smem = (size_t)wpb * wbytes;
-    if (precision == TNMC_F64)
-      TNMC_CUDA_TRY(cudaFuncSetAttribute(sample3d_warp_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    else
-      TNMC_CUDA_TRY(cudaFuncSetAttribute(sample3d_warp_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (force && force[0] == 't') G = 0;
+  if (force && force[0] == 'w') G = 32;
+  if (force && strcmp(force, "group8") == 0) G = 8;
+  if (force && strcmp(force, "group16") == 0) G = 16;
+  // samples per CTA: up to 128 / G, in whole warps, within the shared memory
+  int spb = 0;
+  if (G) {
+    const int per_warp = 32 / G;
+    const int fit = (int)((size_t)max_optin / wbytes);
+    spb = 128 / G < fit ? 128 / G : fit;
+    spb -= spb % per_warp;
+    if (spb < per_warp) G = 0;
   }
   tnmc_status st = TNMC_OK;
   for (int64_t b0 = 0; b0 < B && st == TNMC_OK; b0 += Bc) {
     a.b0 = b0;
     a.Bc = (B - b0) < Bc ? (B - b0) : Bc;
-    if (warp) {
-      const int threads = 32 * wpb;
-      const unsigned blocks = (unsigned)((a.Bc + wpb - 1) / wpb);
-      const size_t smem = (size_t)wpb * wbytes;
-      if (precision == TNMC_F64) sample3d_warp_kernel<double><<<blocks, threads, smem, s>>>(a);
-      else sample3d_warp_kernel<float><<<blocks, threads, smem, s>>>(a);
+    if (G) {
+      const bool f64 = precision == TNMC_F64;
+      st = G == 32 ? (f64 ? launch_group<double, 32>(a, spb, wbytes, s) : launch_group<float, 32>(a, spb, wbytes, s))
+         : G == 16 ? (f64 ? launch_group<double, 16>(a, spb, wbytes, s) : launch_group<float, 16>(a, spb, wbytes, s))
+                   : (f64 ? launch_group<double, 8>(a, spb, wbytes, s) : launch_group<float, 8>(a, spb, wbytes, s));
     } else {
       const int threads = 128;
       const unsigned blocks = (unsigned)((a.Bc + threads - 1) / threads);
       if (precision == TNMC_F64) sample3d_kernel<double><<<blocks, threads, 0, s>>>(a);
       else sample3d_kernel<float><<<blocks, threads, 0, s>>>(a);
-    }
-    if (cudaGetLastError() != cudaSuccess) {
-      tnmc_set_error("3D sampler launch failed");
-      st = TNMC_E_CUDA;
+      if (cudaGetLastError() != cudaSuccess) {
+        tnmc_set_error("3D sampler launch failed");
+        st = TNMC_E_CUDA;
+      }
     }
   }
   dev_free(env->alloc, scr, fbytes + ibytes, s);
