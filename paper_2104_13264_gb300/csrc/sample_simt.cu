@@ -156,9 +156,18 @@ tnmc_status tnmc_launch_sample(const tnmc_env* env, int precision, int64_t B, ui
   if (precision == TNMC_F64)
     return launch_sample_t<double, 64>(env, d.M64, d.R64, d.fe, B, seed, offset, spins_in, spins_out, logq,
                                        energy, flags, stream);
-  if (precision == TNMC_F32)
+  if (precision == TNMC_F32) {
+    // 128 samples per CTA, or 64 when that leaves SMs without a tile (one thread per sample
+    // either way, so every sample's arithmetic is the same)
+    int dev = 0, nsm = 0;
+    TNMC_CUDA_TRY(cudaGetDevice(&dev));
+    TNMC_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    if ((B + 127) / 128 < 2 * (int64_t)nsm)
+      return launch_sample_t<float, 64>(env, d.L32, d.R32, d.fe32, B, seed, offset, spins_in, spins_out, logq,
+                                        energy, flags, stream);
     return launch_sample_t<float, 128>(env, d.L32, d.R32, d.fe32, B, seed, offset, spins_in, spins_out, logq,
                                        energy, flags, stream);
+  }
   if (precision == TNMC_BF16)
     return tnmc_launch_sample_tc(env, B, seed, offset, spins_in, spins_out, logq, energy, flags, stream);
   tnmc_set_error("unknown precision %d", precision);
