@@ -25,7 +25,8 @@ namespace tnmc {
 namespace {
 
 // NT samples per CTA (one per thread); vectors live in shared memory with stride NT + 1
-// (conflict free).  128 up to P = 52; 64 above, so that P = 64 fits the shared memory.
+// (conflict free).  128 up to P = 52 for large batches; 64 above P = 52 (so that P = 64 fits
+// the shared memory) and for batches too small to give every SM two 128-sample tiles.
 
 struct GradArgs {
   DeviceEnv e;
@@ -257,7 +258,10 @@ tnmc_status tnmc_launch_logq_grad(const tnmc_env* env, int64_t B, const int8_t* 
   auto smem_of = [&](int nt) {
     return (size_t)7 * d.P * (nt + 1) * sizeof(float) + (size_t)2 * W * nt * sizeof(uint32_t);
   };
-  const int kNT = smem_of(128) <= (size_t)max_optin ? 128 : 64;
+  int nsm = 0;
+  TNMC_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  // 128 samples per CTA; 64 when P > 52 (shared memory) or when 128 would leave SMs idle
+  const int kNT = (smem_of(128) <= (size_t)max_optin && (B + 127) / 128 >= 2 * (int64_t)nsm) ? 128 : 64;
   const size_t smem = smem_of(kNT);
   if (smem > (size_t)max_optin) {
     tnmc_set_error("gradient kernel needs %zu bytes of shared memory (device allows %d)", smem, max_optin);
