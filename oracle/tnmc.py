@@ -329,8 +329,9 @@ def init_chains(env, C, seed):
 def mh_accept(beta, lq_prop, E_prop, lq_cur, E_cur, u):
     """Metropolis-Hastings rule of eq. mh-acc with g(w'|w) = q(w') (eq. tns-prior).
 
-    Delta = -beta (E' - E) + log q(cur) - log q(prop); accept iff the proposal
-    is valid (finite log q) and u < exp(min(0, Delta)).
+    Delta = log pi(prop) q(cur) / (pi(cur) q(prop)) = a(prop) - a(cur) with
+    a = -beta E - log q (each a rounded once, then the difference); accept iff the
+    proposal is valid (finite log q) and u < exp(min(0, Delta)).
 
     A current state with log q = -inf lies outside the numerical support of q
     (only the random start of Algorithm 1 can be such a state: every later state
@@ -340,7 +341,7 @@ def mh_accept(beta, lq_prop, E_prop, lq_cur, E_cur, u):
     leave its start.  The rule only changes the transient out of the start.
     """
     with np.errstate(invalid="ignore", over="ignore"):
-        d = -beta * (E_prop - E_cur) + (lq_cur - lq_prop)
+        d = (-beta * E_prop - lq_prop) - (-beta * E_cur - lq_cur)
         ok = np.isfinite(lq_prop) & ~np.isnan(d)
         start = np.isneginf(lq_cur)
         return ok & (start | (u < np.exp(np.minimum(np.where(ok & ~start, d, 0.0), 0.0))))

@@ -103,12 +103,15 @@ __global__ void mh_batched_scan_kernel(const MhInst* __restrict__ inst, int64_t 
   const uint64_t seed = params[0];
   const uint64_t t0 = ((uint64_t)i << kSampleOffsetShift) + params[1] * (uint64_t)I.T;
   double lq = chain_logq[g], E = chain_E[g];
+  // Delta = a(prop) - a(cur), a = -beta E - log q, each step rounded once (eq. mh-acc)
+  double wc = __dsub_rn(__dmul_rn(-I.beta, E), lq);
   int64_t lastj = -1, cnt = 0;
   for (int64_t j = 0; j < I.T; ++j) {
     const int64_t row = I.prop_row + c * I.T + j;
     const double u = mh_uniform(seed, t0 + (uint64_t)j, (uint32_t)c);
     const double lqt = prop_logq[row], Et = prop_E[row];
-    const double d = -I.beta * (Et - E) + (lq - lqt);
+    const double wt = __dsub_rn(__dmul_rn(-I.beta, Et), lqt);
+    const double d = __dsub_rn(wt, wc);
     const bool ok = isfinite(lqt) && !isnan(d);
     // a state with log q = -inf (only a random start can be one) takes the first valid proposal
     const bool acc = ok && (lq == -INFINITY || u < exp(fmin(d, 0.0)));
@@ -116,6 +119,7 @@ __global__ void mh_batched_scan_kernel(const MhInst* __restrict__ inst, int64_t 
     if (acc) {
       lq = lqt;
       E = Et;
+      wc = wt;
       lastj = c * I.T + j;
       ++cnt;
     }
