@@ -26,108 +26,187 @@ __device__ __forceinline__ bool mh_below(double u, double d) {
   return u < exp(d);
 }
 
-// The MH uniforms of every (chain, proposal), drawn in parallel: they do not depend on the
-// chain state, so the sequential scan below only carries the dependent arithmetic.
-// Also the log target-over-proposal weight a = -beta E - log q of every proposal (rounded
-// once each step, no contraction), so that Delta = a(prop) - a(cur) is one subtraction.
+// The log target-over-proposal weight a = -beta E - log q of a state (each step rounded
+// once, no contraction), so that Delta = a(prop) - a(cur) is one subtraction.
 __device__ __forceinline__ double mh_weight(double beta, double E, double lq) {
   return __dsub_rn(__dmul_rn(-beta, E), lq);
 }
 
-__global__ void mh_uniforms_kernel(int64_t C, int64_t T, uint64_t seed, uint64_t step_offset, double beta,
-                                   const double* __restrict__ prop_logq, const double* __restrict__ prop_E,
-                                   double* u, double* w) {
+// The rule itself, in FP64: proposal t of chain i against the current weight wc.  A state
+// with log q = -inf (only a random start can be one) takes the first valid proposal.
+__device__ __noinline__ bool mh_exact(double beta, uint64_t seed, uint64_t step, uint32_t chain, double lqt,
+                                      double Et, double wc, bool start) {
+  const double d = __dsub_rn(mh_weight(beta, Et, lqt), wc);
+  const bool ok = isfinite(lqt) && !isnan(d);
+  return ok && (start || mh_below(mh_uniform(seed, step, chain), d));
+}
+
+// Order-preserving map of the doubles (NaN excluded) onto int64: key(x) <= key(y) implies
+// x <= y, and x < y implies key(x) < key(y).
+__device__ __forceinline__ int64_t mh_key(double x) {
+  const int64_t b = __double_as_longlong(x);
+  return b >= 0 ? b : (b ^ INT64_MAX);
+}
+__device__ __forceinline__ double mh_unkey(int64_t k) { return __longlong_as_double(k >= 0 ? k : (k ^ INT64_MAX)); }
+
+// Per proposal, in parallel (nothing here depends on the chain state): its weight key kt and
+// an acceptance band on the current weight wc, so that the sequential scan decides with two
+// integer compares:
+//   key(wc) <= lo  -> accept,   key(wc) >= hi  -> reject,   otherwise the FP64 rule.
+// With theta = a' - log u (the wc at which Delta = log u), lo = max(key(theta - m), kt),
+// hi = key(theta + m), m = 1e-12 (1 + |theta|):
+//   - wc <= a' gives Delta >= 0 (the rounded difference keeps the sign): accepted.
+//   - |wc - theta| >= m puts Delta at least 9.9e-13 away from log u, while the roundings of
+//     log u, theta and Delta and the error of exp (|log u| <= 36.8 since u >= 2^-53) sum to
+//     below 1e-14, so u < exp(Delta) has the answer the side of theta says.
+// A proposal with non-finite log q is never accepted (lo = hi = INT64_MIN); u = 0 or a
+// non-finite weight leaves every wc to the FP64 rule (lo = INT64_MIN, hi = INT64_MAX).
+__global__ void mh_bands_kernel(int64_t C, int64_t T, uint64_t seed, uint64_t step_offset, double beta,
+                                const double* __restrict__ prop_logq, const double* __restrict__ prop_E,
+                                int64_t* __restrict__ band_lo, int64_t* __restrict__ band_hi,
+                                int64_t* __restrict__ key_w) {
   const int64_t total = C * T;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = t / T, j = t % T;
-    u[t] = mh_uniform(seed, step_offset + (uint64_t)j, (uint32_t)i);
-    w[t] = mh_weight(beta, prop_E[t], prop_logq[t]);
+    const double lqt = prop_logq[t];
+    const double wt = mh_weight(beta, prop_E[t], lqt);
+    const int64_t kt = mh_key(wt);
+    int64_t lo = INT64_MIN, hi = INT64_MIN;
+    if (isfinite(lqt)) {
+      const double u = mh_uniform(seed, step_offset + (uint64_t)j, (uint32_t)i);
+      hi = INT64_MAX;
+      if (isfinite(wt) && u > 0.0) {
+        const double theta = wt - log(u);
+        const double m = 1e-12 * (1.0 + fabs(theta));
+        const int64_t kl = mh_key(theta - m);
+        lo = kl > kt ? kl : kt;
+        hi = mh_key(theta + m);
+      }
+    }
+    band_lo[t] = lo;
+    band_hi[t] = hi;
+    key_w[t] = kt;
   }
 }
 
-// One thread per chain, sequential over its T proposals (proposal t = i*T + j), with the
-// uniforms u[t] precomputed.
-__global__ void mh_scan_kernel(int64_t C, int64_t T, double beta, const double* __restrict__ prop_logq,
-                               const double* __restrict__ prop_E, const double* __restrict__ u_all,
-                               const double* __restrict__ w_all, double* __restrict__ chain_logq,
+// One thread per chain, sequential over its T proposals (proposal t = i*T + j).  `slow`
+// (a random start, or a current weight that is NaN) sends every decision to the FP64 rule
+// until the first acceptance.
+__global__ void mh_scan_kernel(int64_t C, int64_t T, double beta, uint64_t seed, uint64_t step_offset,
+                               const double* __restrict__ prop_logq, const double* __restrict__ prop_E,
+                               const int64_t* __restrict__ band_lo, const int64_t* __restrict__ band_hi,
+                               const int64_t* __restrict__ key_w, double* __restrict__ chain_logq,
                                double* __restrict__ chain_E, uint8_t* __restrict__ accepted,
                                int64_t* __restrict__ last, int64_t* n_accepted) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= C) return;
-  double lq = chain_logq[i], E = chain_E[i];
-  double wc = mh_weight(beta, E, lq);
+  const double lq0 = chain_logq[i];
+  const double w0 = mh_weight(beta, chain_E[i], lq0);
+  bool start = lq0 == -INFINITY, slow = start || isnan(w0);
+  int64_t kc = mh_key(w0);
   int64_t lastt = -1, cnt = 0;
 #pragma unroll 4
   for (int64_t j = 0; j < T; ++j) {
     const int64_t t = i * T + j;
-    const double u = u_all[t];
-    const double lqt = prop_logq[t], Et = prop_E[t], wt = w_all[t];
-    const double d = __dsub_rn(wt, wc);
-    const bool ok = isfinite(lqt) && !isnan(d);
-    // a state with log q = -inf (only a random start can be one) takes the first valid proposal
-    const bool acc = ok && (lq == -INFINITY || mh_below(u, d));
+    const int64_t lo = band_lo[t], hi = band_hi[t], kt = key_w[t];
+    bool acc;
+    if (!slow && kc <= lo) acc = true;
+    else if (!slow && kc >= hi) acc = false;
+    else acc = mh_exact(beta, seed, step_offset + (uint64_t)j, (uint32_t)i, prop_logq[t], prop_E[t],
+                        mh_unkey(kc), start);
     if (accepted) accepted[t] = acc ? 1 : 0;
     if (acc) {
-      lq = lqt;
-      E = Et;
-      wc = wt;
+      kc = kt;
+      start = slow = false;
       lastt = t;
       ++cnt;
     }
   }
-  chain_logq[i] = lq;
-  chain_E[i] = E;
+  if (lastt >= 0) {
+    chain_logq[i] = prop_logq[lastt];
+    chain_E[i] = prop_E[lastt];
+  }
   last[i] = lastt;
   if (n_accepted && cnt) atomicAdd(reinterpret_cast<unsigned long long*>(n_accepted), (unsigned long long)cnt);
 }
 
-// The same scan with one warp per chain: the lanes load 32 proposals at a time, each
-// proposal's values are broadcast by shuffle, and every lane takes the decision with the
-// arithmetic of mh_scan_kernel (so the decisions are identical); the loads of a block of
-// 32 proceed together instead of one at a time on the dependent chain.
-__global__ void mh_scan_warp_kernel(int64_t C, int64_t T, double beta, const double* __restrict__ prop_logq,
-                                    const double* __restrict__ prop_E, const double* __restrict__ u_all,
-                                    const double* __restrict__ w_all,
-                                    double* __restrict__ chain_logq, double* __restrict__ chain_E,
-                                    uint8_t* __restrict__ accepted, int64_t* __restrict__ last,
-                                    int64_t* n_accepted) {
+// The same scan with one warp per chain: the lanes hold the bands of 128 proposals (4 per
+// lane, coalesced), the next 128 are loaded while the current ones are scanned, and each
+// proposal's band is broadcast by shuffle; every lane takes the same decisions.
+constexpr int kScanR = 4;
+__global__ void mh_scan_warp_kernel(int64_t C, int64_t T, double beta, uint64_t seed, uint64_t step_offset,
+                                    const double* __restrict__ prop_logq, const double* __restrict__ prop_E,
+                                    const int64_t* __restrict__ band_lo, const int64_t* __restrict__ band_hi,
+                                    const int64_t* __restrict__ key_w, double* __restrict__ chain_logq,
+                                    double* __restrict__ chain_E, uint8_t* __restrict__ accepted,
+                                    int64_t* __restrict__ last, int64_t* n_accepted) {
+  constexpr int kBlk = 32 * kScanR;
   const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (i >= C) return;      // warp-uniform
-  double lq = chain_logq[i], E = chain_E[i];
-  double wc = mh_weight(beta, E, lq);
+  const double lq0 = chain_logq[i];
+  const double w0 = mh_weight(beta, chain_E[i], lq0);
+  bool start = lq0 == -INFINITY, slow = start || isnan(w0);
+  int64_t kc = mh_key(w0);
   int64_t lastt = -1, cnt = 0;
-  for (int64_t base = 0; base < T; base += 32) {
-    const int64_t n = (T - base) < 32 ? (T - base) : 32;
-    const int64_t tl = i * T + base + lane;
-    double ul = 0.0, lql = 0.0, El = 0.0, wl = 0.0;
-    if (lane < n) {
-      ul = u_all[tl];
-      lql = prop_logq[tl];
-      El = prop_E[tl];
-      wl = w_all[tl];
+  const int64_t row = i * T;
+  long long lo[kScanR], hi[kScanR], kt[kScanR], nlo[kScanR], nhi[kScanR], nkt[kScanR];
+#pragma unroll
+  for (int r = 0; r < kScanR; ++r) {
+    const int64_t j = r * 32 + lane;
+    const bool in = j < T;
+    lo[r] = in ? band_lo[row + j] : 0;
+    hi[r] = in ? band_hi[row + j] : 0;
+    kt[r] = in ? key_w[row + j] : 0;
+  }
+  for (int64_t base = 0; base < T; base += kBlk) {
+#pragma unroll
+    for (int r = 0; r < kScanR; ++r) {   // the next block's bands, in flight during this one
+      const int64_t j = base + kBlk + r * 32 + lane;
+      const bool in = j < T;
+      nlo[r] = in ? band_lo[row + j] : 0;
+      nhi[r] = in ? band_hi[row + j] : 0;
+      nkt[r] = in ? key_w[row + j] : 0;
     }
-    for (int k = 0; k < (int)n; ++k) {
-      const double u = __shfl_sync(0xffffffffu, ul, k);
-      const double lqt = __shfl_sync(0xffffffffu, lql, k);
-      const double Et = __shfl_sync(0xffffffffu, El, k);
-      const double wt = __shfl_sync(0xffffffffu, wl, k);
-      const double d = __dsub_rn(wt, wc);
-      const bool ok = isfinite(lqt) && !isnan(d);
-      const bool acc = ok && (lq == -INFINITY || mh_below(u, d));
-      if (accepted && lane == k) accepted[tl] = acc ? 1 : 0;
-      if (acc) {
-        lq = lqt;
-        E = Et;
-        wc = wt;
-        lastt = i * T + base + k;
-        ++cnt;
+    bool mine[kScanR];
+#pragma unroll
+    for (int r = 0; r < kScanR; ++r) {
+      mine[r] = false;
+      const int64_t j0 = base + r * 32;
+      const int n = (T - j0) < 32 ? (int)(T - j0) : 32;     // <= 0 past the end
+#pragma unroll 8
+      for (int k = 0; k < n; ++k) {
+        const long long l = __shfl_sync(0xffffffffu, lo[r], k);
+        const long long h = __shfl_sync(0xffffffffu, hi[r], k);
+        const long long w = __shfl_sync(0xffffffffu, kt[r], k);
+        const int64_t j = j0 + k;
+        bool acc;
+        if (!slow && kc <= l) acc = true;
+        else if (!slow && kc >= h) acc = false;
+        else acc = mh_exact(beta, seed, step_offset + (uint64_t)j, (uint32_t)i, prop_logq[row + j], prop_E[row + j],
+                            mh_unkey(kc), start);
+        if (lane == k) mine[r] = acc;
+        if (acc) {
+          kc = w;
+          start = slow = false;
+          lastt = row + j;
+          ++cnt;
+        }
       }
+      if (accepted && lane < n) accepted[row + j0 + lane] = mine[r] ? 1 : 0;
+    }
+#pragma unroll
+    for (int r = 0; r < kScanR; ++r) {
+      lo[r] = nlo[r];
+      hi[r] = nhi[r];
+      kt[r] = nkt[r];
     }
   }
   if (lane == 0) {
-    chain_logq[i] = lq;
-    chain_E[i] = E;
+    if (lastt >= 0) {
+      chain_logq[i] = prop_logq[lastt];
+      chain_E[i] = prop_E[lastt];
+    }
     last[i] = lastt;
     if (n_accepted && cnt) atomicAdd(reinterpret_cast<unsigned long long*>(n_accepted), (unsigned long long)cnt);
   }
@@ -175,26 +254,30 @@ tnmc_status tnmc_launch_mh_core(int64_t n, double beta, const tnmc::Allocator& a
                                 uint64_t step_offset, uint8_t* accepted, int64_t* n_accepted, cudaStream_t stream) {
   using namespace tnmc;
   if (C == 0 || T == 0) return TNMC_OK;
-  const size_t bytes = (size_t)C * sizeof(int64_t) + (size_t)C * T * 2 * sizeof(double);
+  const size_t bytes = (size_t)C * sizeof(int64_t) + (size_t)C * T * 3 * sizeof(int64_t);
   char* buf = static_cast<char*>(dev_alloc(alloc, bytes, stream));
   if (!buf) {
     tnmc_set_error("cannot allocate %zu bytes for the MH scan", bytes);
     return TNMC_E_NOMEM;
   }
-  double* u = reinterpret_cast<double*>(buf);
-  double* w = u + (size_t)C * T;
-  int64_t* last = reinterpret_cast<int64_t*>(buf + (size_t)C * T * 2 * sizeof(double));
-  mh_uniforms_kernel<<<1024, 256, 0, stream>>>(C, T, seed, step_offset, beta, prop_logq, prop_energy, u, w);
+  int64_t* band_lo = reinterpret_cast<int64_t*>(buf);
+  int64_t* band_hi = band_lo + (size_t)C * T;
+  int64_t* key_w = band_hi + (size_t)C * T;
+  int64_t* last = key_w + (size_t)C * T;
+  mh_bands_kernel<<<1024, 256, 0, stream>>>(C, T, seed, step_offset, beta, prop_logq, prop_energy, band_lo, band_hi,
+                                            key_w);
   TNMC_CUDA_TRY(cudaGetLastError());
   const int threads = 128;
   if (C <= 65536) {   // one warp per chain
     const int64_t blocks = (C * 32 + threads - 1) / threads;
-    mh_scan_warp_kernel<<<(unsigned)blocks, threads, 0, stream>>>(C, T, beta, prop_logq, prop_energy, u, w,
-                                                                  chain_logq, chain_energy, accepted, last, n_accepted);
+    mh_scan_warp_kernel<<<(unsigned)blocks, threads, 0, stream>>>(C, T, beta, seed, step_offset, prop_logq,
+                                                                  prop_energy, band_lo, band_hi, key_w, chain_logq,
+                                                                  chain_energy, accepted, last, n_accepted);
   } else {            // one thread per chain
     const int64_t blocks = (C + threads - 1) / threads;
-    mh_scan_kernel<<<(unsigned)blocks, threads, 0, stream>>>(C, T, beta, prop_logq, prop_energy, u, w, chain_logq,
-                                                             chain_energy, accepted, last, n_accepted);
+    mh_scan_kernel<<<(unsigned)blocks, threads, 0, stream>>>(C, T, beta, seed, step_offset, prop_logq, prop_energy,
+                                                             band_lo, band_hi, key_w, chain_logq, chain_energy,
+                                                             accepted, last, n_accepted);
   }
   TNMC_CUDA_TRY(cudaGetLastError());
   const int64_t cb = C < 65535 ? C : 65535;
