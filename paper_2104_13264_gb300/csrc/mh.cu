@@ -89,9 +89,70 @@ __global__ void mh_bands_kernel(int64_t C, int64_t T, uint64_t seed, uint64_t st
   }
 }
 
-// One thread per chain, sequential over its T proposals (proposal t = i*T + j).  `slow`
-// (a random start, or a current weight that is NaN) sends every decision to the FP64 rule
+// The state a chain carries through the scan: its weight key, and whether it sits at a
+// random start (log q = -inf) or at a NaN weight, where every decision takes the FP64 rule
 // until the first acceptance.
+struct ScanState {
+  int64_t kc;
+  bool start, slow;
+};
+
+// Decides proposals j0 .. j0+cnt-1 (cnt <= kGrp) of one chain from their bands, held in
+// registers.  A speculative pass takes every decision by the compares alone (a compare and
+// a select per proposal on the dependent path); if one of them falls inside its band, or the
+// chain is slow, the group is decided again from its entry state, with the FP64 rule where
+// the band leaves it open.  Returns the group's acceptance bits.
+constexpr int kGrp = 8;
+__device__ __forceinline__ uint32_t mh_group(ScanState& st, const long long (&l)[kGrp], const long long (&h)[kGrp],
+                                             const long long (&w)[kGrp], int cnt, double beta, uint64_t seed,
+                                             uint64_t step0, uint32_t chain, const double* lq_row,
+                                             const double* E_row) {
+  int64_t kc = st.kc;
+  bool unc = st.slow;
+  uint32_t m = 0;
+#pragma unroll
+  for (int g = 0; g < kGrp; ++g) {
+    const bool in = g < cnt;
+    const bool a = in && kc <= l[g];
+    unc |= in && !a && kc < h[g];
+    kc = a ? w[g] : kc;
+    m |= (uint32_t)a << g;
+  }
+  if (!unc) {
+    st.kc = kc;
+    return m;
+  }
+  kc = st.kc;
+  m = 0;
+#pragma unroll
+  for (int g = 0; g < kGrp; ++g) {
+    if (g < cnt) {
+      bool a;
+      if (!st.slow && kc <= l[g]) a = true;
+      else if (!st.slow && kc >= h[g]) a = false;
+      else a = mh_exact(beta, seed, step0 + (uint64_t)g, chain, lq_row[g], E_row[g], mh_unkey(kc), st.start);
+      if (a) {
+        kc = w[g];
+        st.start = st.slow = false;
+      }
+      m |= (uint32_t)a << g;
+    }
+  }
+  st.kc = kc;
+  return m;
+}
+
+__device__ __forceinline__ ScanState mh_scan_start(double beta, double lq0, double E0) {
+  const double w0 = mh_weight(beta, E0, lq0);
+  ScanState st;
+  st.kc = mh_key(w0);
+  st.start = lq0 == -INFINITY;
+  st.slow = st.start || isnan(w0);
+  return st;
+}
+
+// One thread per chain, sequential over its T proposals (proposal t = i*T + j), in groups of
+// kGrp whose bands are loaded together.
 __global__ void mh_scan_kernel(int64_t C, int64_t T, double beta, uint64_t seed, uint64_t step_offset,
                                const double* __restrict__ prop_logq, const double* __restrict__ prop_E,
                                const int64_t* __restrict__ band_lo, const int64_t* __restrict__ band_hi,
@@ -100,26 +161,29 @@ __global__ void mh_scan_kernel(int64_t C, int64_t T, double beta, uint64_t seed,
                                int64_t* __restrict__ last, int64_t* n_accepted) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= C) return;
-  const double lq0 = chain_logq[i];
-  const double w0 = mh_weight(beta, chain_E[i], lq0);
-  bool start = lq0 == -INFINITY, slow = start || isnan(w0);
-  int64_t kc = mh_key(w0);
+  ScanState st = mh_scan_start(beta, chain_logq[i], chain_E[i]);
+  const int64_t row = i * T;
   int64_t lastt = -1, cnt = 0;
-#pragma unroll 4
-  for (int64_t j = 0; j < T; ++j) {
-    const int64_t t = i * T + j;
-    const int64_t lo = band_lo[t], hi = band_hi[t], kt = key_w[t];
-    bool acc;
-    if (!slow && kc <= lo) acc = true;
-    else if (!slow && kc >= hi) acc = false;
-    else acc = mh_exact(beta, seed, step_offset + (uint64_t)j, (uint32_t)i, prop_logq[t], prop_E[t],
-                        mh_unkey(kc), start);
-    if (accepted) accepted[t] = acc ? 1 : 0;
-    if (acc) {
-      kc = kt;
-      start = slow = false;
-      lastt = t;
-      ++cnt;
+  for (int64_t j0 = 0; j0 < T; j0 += kGrp) {
+    const int n = (T - j0) < kGrp ? (int)(T - j0) : kGrp;
+    long long l[kGrp], h[kGrp], w[kGrp];
+#pragma unroll
+    for (int g = 0; g < kGrp; ++g) {
+      const bool in = g < n;
+      l[g] = in ? band_lo[row + j0 + g] : 0;
+      h[g] = in ? band_hi[row + j0 + g] : 0;
+      w[g] = in ? key_w[row + j0 + g] : 0;
+    }
+    const uint32_t m = mh_group(st, l, h, w, n, beta, seed, step_offset + (uint64_t)j0, (uint32_t)i,
+                                prop_logq + row + j0, prop_E + row + j0);
+    if (m) {
+      cnt += __popc(m);
+      lastt = row + j0 + (31 - __clz(m));
+    }
+    if (accepted) {
+#pragma unroll
+      for (int g = 0; g < kGrp; ++g)
+        if (g < n) accepted[row + j0 + g] = (m >> g) & 1u;
     }
   }
   if (lastt >= 0) {
@@ -130,27 +194,30 @@ __global__ void mh_scan_kernel(int64_t C, int64_t T, double beta, uint64_t seed,
   if (n_accepted && cnt) atomicAdd(reinterpret_cast<unsigned long long*>(n_accepted), (unsigned long long)cnt);
 }
 
-// The same scan with one warp per chain: the lanes hold the bands of 128 proposals (4 per
-// lane, coalesced), the next 128 are loaded while the current ones are scanned, and each
-// proposal's band is broadcast by shuffle; every lane takes the same decisions.
+// The same scan with one warp per chain, for up to 65536 chains: the lanes load the bands of
+// 128 proposals (4 per lane, coalesced) and stage them in the warp's shared memory; the next
+// 128 are loaded while these are scanned.  Every lane runs the scan on the staged bands (the
+// same values, read by broadcast), lanes 0-7 record each group's acceptance bits, and the
+// flags of the 128 leave in one coalesced store.
 constexpr int kScanR = 4;
-__global__ void mh_scan_warp_kernel(int64_t C, int64_t T, double beta, uint64_t seed, uint64_t step_offset,
-                                    const double* __restrict__ prop_logq, const double* __restrict__ prop_E,
-                                    const int64_t* __restrict__ band_lo, const int64_t* __restrict__ band_hi,
-                                    const int64_t* __restrict__ key_w, double* __restrict__ chain_logq,
-                                    double* __restrict__ chain_E, uint8_t* __restrict__ accepted,
-                                    int64_t* __restrict__ last, int64_t* n_accepted) {
+constexpr int kScanWarps = 4;
+__global__ void __launch_bounds__(32 * kScanWarps)
+    mh_scan_warp_kernel(int64_t C, int64_t T, double beta, uint64_t seed, uint64_t step_offset,
+                        const double* __restrict__ prop_logq, const double* __restrict__ prop_E,
+                        const int64_t* __restrict__ band_lo, const int64_t* __restrict__ band_hi,
+                        const int64_t* __restrict__ key_w, double* __restrict__ chain_logq,
+                        double* __restrict__ chain_E, uint8_t* __restrict__ accepted,
+                        int64_t* __restrict__ last, int64_t* n_accepted) {
   constexpr int kBlk = 32 * kScanR;
+  __shared__ long long s_band[kScanWarps][3][kBlk];
+  __shared__ uint8_t s_acc[kScanWarps][kBlk];
   const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (i >= C) return;      // warp-uniform
-  const double lq0 = chain_logq[i];
-  const double w0 = mh_weight(beta, chain_E[i], lq0);
-  bool start = lq0 == -INFINITY, slow = start || isnan(w0);
-  int64_t kc = mh_key(w0);
+  ScanState st = mh_scan_start(beta, chain_logq[i], chain_E[i]);
   int64_t lastt = -1, cnt = 0;
   const int64_t row = i * T;
-  long long lo[kScanR], hi[kScanR], kt[kScanR], nlo[kScanR], nhi[kScanR], nkt[kScanR];
+  long long lo[kScanR], hi[kScanR], kt[kScanR];
 #pragma unroll
   for (int r = 0; r < kScanR; ++r) {
     const int64_t j = r * 32 + lane;
@@ -160,46 +227,47 @@ __global__ void mh_scan_warp_kernel(int64_t C, int64_t T, double beta, uint64_t 
     kt[r] = in ? key_w[row + j] : 0;
   }
   for (int64_t base = 0; base < T; base += kBlk) {
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < kScanR; ++r) {
+      s_band[wid][0][r * 32 + lane] = lo[r];
+      s_band[wid][1][r * 32 + lane] = hi[r];
+      s_band[wid][2][r * 32 + lane] = kt[r];
+    }
+    __syncwarp();
 #pragma unroll
     for (int r = 0; r < kScanR; ++r) {   // the next block's bands, in flight during this one
       const int64_t j = base + kBlk + r * 32 + lane;
       const bool in = j < T;
-      nlo[r] = in ? band_lo[row + j] : 0;
-      nhi[r] = in ? band_hi[row + j] : 0;
-      nkt[r] = in ? key_w[row + j] : 0;
+      lo[r] = in ? band_lo[row + j] : 0;
+      hi[r] = in ? band_hi[row + j] : 0;
+      kt[r] = in ? key_w[row + j] : 0;
     }
-    bool mine[kScanR];
+    const int n = (T - base) < kBlk ? (int)(T - base) : kBlk;
+    for (int k = 0; k < n; k += kGrp) {
+      long long l[kGrp], h[kGrp], w[kGrp];
 #pragma unroll
-    for (int r = 0; r < kScanR; ++r) {
-      mine[r] = false;
-      const int64_t j0 = base + r * 32;
-      const int n = (T - j0) < 32 ? (int)(T - j0) : 32;     // <= 0 past the end
-#pragma unroll 8
-      for (int k = 0; k < n; ++k) {
-        const long long l = __shfl_sync(0xffffffffu, lo[r], k);
-        const long long h = __shfl_sync(0xffffffffu, hi[r], k);
-        const long long w = __shfl_sync(0xffffffffu, kt[r], k);
-        const int64_t j = j0 + k;
-        bool acc;
-        if (!slow && kc <= l) acc = true;
-        else if (!slow && kc >= h) acc = false;
-        else acc = mh_exact(beta, seed, step_offset + (uint64_t)j, (uint32_t)i, prop_logq[row + j], prop_E[row + j],
-                            mh_unkey(kc), start);
-        if (lane == k) mine[r] = acc;
-        if (acc) {
-          kc = w;
-          start = slow = false;
-          lastt = row + j;
-          ++cnt;
-        }
+      for (int g = 0; g < kGrp; ++g) {
+        l[g] = s_band[wid][0][k + g];
+        h[g] = s_band[wid][1][k + g];
+        w[g] = s_band[wid][2][k + g];
       }
-      if (accepted && lane < n) accepted[row + j0 + lane] = mine[r] ? 1 : 0;
+      const int c = (n - k) < kGrp ? (n - k) : kGrp;
+      const uint32_t m = mh_group(st, l, h, w, c, beta, seed, step_offset + (uint64_t)(base + k), (uint32_t)i,
+                                  prop_logq + row + base + k, prop_E + row + base + k);
+      if (m) {
+        cnt += __popc(m);
+        lastt = row + base + k + (31 - __clz(m));
+      }
+      if (lane < kGrp) s_acc[wid][k + lane] = (m >> lane) & 1u;
     }
+    __syncwarp();
+    if (accepted) {
 #pragma unroll
-    for (int r = 0; r < kScanR; ++r) {
-      lo[r] = nlo[r];
-      hi[r] = nhi[r];
-      kt[r] = nkt[r];
+      for (int r = 0; r < kScanR; ++r) {
+        const int j = r * 32 + lane;
+        if (j < n) accepted[row + base + j] = s_acc[wid][j];
+      }
     }
   }
   if (lane == 0) {
@@ -267,7 +335,7 @@ tnmc_status tnmc_launch_mh_core(int64_t n, double beta, const tnmc::Allocator& a
   mh_bands_kernel<<<1024, 256, 0, stream>>>(C, T, seed, step_offset, beta, prop_logq, prop_energy, band_lo, band_hi,
                                             key_w);
   TNMC_CUDA_TRY(cudaGetLastError());
-  const int threads = 128;
+  const int threads = 128;   // 4 warps: the warp form's shared-memory layout
   if (C <= 65536) {   // one warp per chain
     const int64_t blocks = (C * 32 + threads - 1) / threads;
     mh_scan_warp_kernel<<<(unsigned)blocks, threads, 0, stream>>>(C, T, beta, seed, step_offset, prop_logq,
