@@ -279,14 +279,19 @@ tnmc_status tnmc_init_chains(const tnmc_env* env, int precision, int64_t C, uint
 /*
  * Metropolis-Hastings scan (eq. mh-acc with g(w'|w) = q(w'), Algorithm 1):
  * chain i consumes proposals i*T .. i*T+T-1 in order.  For proposal t
- *   Delta = -beta (E_t - E_cur) + log q_cur - log q_t,
+ *   Delta = a_t - a_cur,  a = (-beta * E) - log q  (each operation rounded once),
  *   accept iff log q_t is finite and u < exp(min(0, Delta)),
- * u from the MH stream at step (step_offset + j).  On exit each chain holds
- * its last accepted proposal (spins, log q, energy).
+ * u from the MH stream at step (step_offset + j).  A chain whose log q is -inf
+ * (a random start outside q's support) takes its first valid proposal.  On exit
+ * each chain holds its last accepted proposal (spins, log q, energy).  The
+ * decisions are those of the FP64 rule, most of them taken by integer compares
+ * against per-proposal bands computed beforehand.
  * prop_*      device [C*T] (spins [C*T][Ly][Lx])
  * chain_*     device [C] in/out (spins [C][Ly][Lx])
  * accepted    device uint8 [C*T] or NULL (output)
  * n_accepted  device int64 scalar or NULL; the number accepted is ADDED to it
+ * Scratch: 24 C T + 8 C bytes from the env's allocator (TNMC_E_NOMEM if refused),
+ * freed on the stream before return.
  */
 tnmc_status tnmc_mh_step(const tnmc_env* env, int64_t C, int64_t T, const int8_t* prop_spins,
                          const double* prop_logq, const double* prop_energy, int8_t* chain_spins,
