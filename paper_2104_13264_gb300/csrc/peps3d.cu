@@ -1515,7 +1515,8 @@ static tnmc_status build3d(const tnmc_lattice3d* lat, double beta, int D, int ch
   } while (0);
   if (work) dev_free(env->alloc, work, wbytes, s);
   if (st != TNMC_OK) {
-    tnmc_set_error("3D build failed: %s", cudaGetErrorString(cudaGetLastError()));
+    // a refused allocation keeps its own message
+    if (st == TNMC_E_CUDA) tnmc_set_error("3D build failed: %s", cudaGetErrorString(cudaGetLastError()));
     (void)cudaStreamSynchronize(s);
     dev_free(env->alloc, base, off, s);
     delete env;
