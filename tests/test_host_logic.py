@@ -66,3 +66,35 @@ def test_open_instances_match_the_oracle_cut():
                 assert list(a[0]) == list(b[0]) and list(a[1]) == list(b[1])
                 for x, y in zip(a[2:], b[2:]):
                     np.testing.assert_allclose(x, y, rtol=0, atol=1e-13)
+
+
+def _bench_module():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+@pytest.mark.parametrize("gauge", ["spin", "bond"])
+def test_roofline_flop_count_uses_the_built_bond_dimensions(gauge):
+    """The roofline's algorithmic FLOPs per sample (8 chi_c chi_{c+1} per site, 4 on row 0)
+    model the sampling bonds as min(chi, 2^min(c, Lx - c, Ly - r)) (doubled in the bond
+    basis). They must equal the same sum over the bonds of the environments the oracle
+    actually builds, on random instances whose bonds saturate in some rows and not in others."""
+    from types import SimpleNamespace
+
+    import numpy as np
+
+    from oracle import tnmc
+    bench = _bench_module()
+    r = np.random.default_rng(0)
+    build = tnmc.build_env if gauge == "spin" else tnmc.build_env_bond
+    for Ly, Lx, chi in ((6, 7, 4), (5, 9, 3), (4, 4, 16), (3, 10, 2), (2, 1, 4)):
+        Jh, Jv = r.standard_normal((Ly, Lx - 1)), r.standard_normal((Ly - 1, Lx))
+        h = 0.3 * r.standard_normal((Ly, Lx))
+        env = build(Jh, Jv, h, 0.7, chi)
+        built = sum((8 if row > 0 else 4) * env.M[row][c].shape[0] * env.M[row][c].shape[2]
+                    for row in range(Ly) for c in range(Lx))
+        model = bench.algorithmic_flops(SimpleNamespace(Lx=Lx, Ly=Ly, chi=chi), gauge=gauge)
+        assert model == built, (Ly, Lx, chi, model, built)
