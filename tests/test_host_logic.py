@@ -98,3 +98,43 @@ def test_roofline_flop_count_uses_the_built_bond_dimensions(gauge):
                     for row in range(Ly) for c in range(Lx))
         model = bench.algorithmic_flops(SimpleNamespace(Lx=Lx, Ly=Ly, chi=chi), gauge=gauge)
         assert model == built, (Ly, Lx, chi, model, built)
+
+
+def test_mh_band_margin_is_sound():
+    """The MH scan's integer bands (order-preserving int64 keys of the weights a; accept on
+    key(a) <= max(key(theta - m), key(a')), reject on key(a) >= key(theta + m), with
+    theta = a' - log u and m = 1e-12 (1 + |theta|)) never contradict the rule
+    u < exp(min(0, a' - a)) evaluated in FP64, here with numpy's log and exp, for current
+    weights placed at chosen multiples of m from theta and weights of magnitude 1 to 1e7.
+    This checks the margin argument; the kernels themselves are compared with the oracle's
+    rule on the GPU."""
+    import numpy as np
+    i64max = np.int64(2 ** 63 - 1)
+
+    def key(x):
+        b = np.asarray(x, dtype=np.float64).view(np.int64)
+        return np.where(b >= 0, b, b ^ i64max)
+
+    rng = np.random.default_rng(1)
+    n = 250_000
+    decided = 0
+    for scale in (1.0, 1e3, 1e5, 1e7):
+        u = rng.integers(1, 2 ** 53, n) * 2.0 ** -53
+        u[:10] = 1 - 2.0 ** -53
+        u[10:20] = 2.0 ** -53
+        wt = rng.normal(0.0, scale, n)
+        theta = wt - np.log(u)
+        m = 1e-12 * (1.0 + np.abs(theta))
+        k = rng.choice([-5, -2, -1.01, -1, -0.5, 0, 0.5, 1, 1.01, 2, 5, 1e6, -1e6], n)
+        wc = theta + k * m
+        lo = np.maximum(key(theta - m), key(wt))
+        hi = key(theta + m)
+        kc = key(wc)
+        acc, rej = kc <= lo, (kc >= hi) & ~(kc <= lo)
+        with np.errstate(over="ignore"):
+            d = wt - wc
+            rule = (d >= 0) | (u < np.exp(np.minimum(d, 0.0)))
+        assert not np.any(acc & ~rule), scale
+        assert not np.any(rej & rule), scale
+        decided += int(np.sum(acc | rej))
+    assert decided > 0.7 * 4 * n       # most placements fall outside the band
